@@ -1,0 +1,324 @@
+#!/usr/bin/env python
+"""Benchmark of the MCL expansion hot path on GB300.
+
+A step is one whole MCL iteration through the C ABI (mcl_expand):
+expansion A*A fused with prune / top-k select / recovery, inflation,
+FP64 renormalisation and chaos, on the 1M-vertex power-law workload
+(Zipf(2) degrees, mean ~50, capped at 5,000; ~49M nnz; lognormal(0,1)
+weights; self-loops; column-stochastic).  value = expansion GFLOP/s
+(2 x multiply-adds / step time), whole job.  The path does not shard:
+with --gpus N each rank runs an independent replica (weak scaling).
+
+--impl reference times the FP64 CPU oracle on the host cores on bounded
+column samples of the same workload (the only CPU code bench.py runs
+besides the cpu_baseline leg of the default arm).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "expansion GFLOP/s & MCL iters/s, learned+batched vs plain, 1 GB300 at 1e-5"
+WORKLOAD = ("zipf1m: one MCL iteration (expand + prune theta=1e-4 / select k=1100 / recover 90% "
+            "+ inflate r=2 + renormalise + chaos) on a 1M-vertex Zipf(2) power-law graph, "
+            "mean degree ~50 capped at 5,000, lognormal(0,1) weights, int32 CSC, seed 0")
+PARAMS = dict(threshold=1e-4, select_k=1100, recover_pct=0.9, inflation=2.0)
+
+
+def _env_rank():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)),
+            int(os.environ.get("WORLD_SIZE", 1)))
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: str):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", self.idx], stdout=subprocess.PIPE,
+                stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def make_workload(name: str, seed: int = 0):
+    from paper_2002_10083_gb300 import synth
+    cache = os.environ.get("MCL_BENCH_CACHE", "/tmp/mcl_bench_cache")
+    path = os.path.join(cache, f"{name}_s{seed}.npz")
+    if os.path.exists(path):
+        z = np.load(path)
+        return synth.CSC(n=int(z["n"]), colptr=z["colptr"], rowidx=z["rowidx"], val=z["val"])
+    A = synth.config(name, seed=seed)
+    A = synth.CSC(n=A.n, colptr=A.colptr, rowidx=A.rowidx, val=A.val.astype(np.float32))
+    try:
+        os.makedirs(cache, exist_ok=True)
+        np.savez(path + ".tmp.npz", n=A.n, colptr=A.colptr, rowidx=A.rowidx, val=A.val)
+        os.replace(path + ".tmp.npz", path)
+    except Exception:
+        pass
+    return A
+
+
+def oracle_gflops(A, seconds: float, seed: int = 1):
+    """The FP64 oracle as it stands on random column samples: GFLOP/s."""
+    import oracle
+    prm = oracle.Params(theta=float(np.float32(PARAMS["threshold"])), K=PARAMS["select_k"],
+                        p=float(np.float32(PARAMS["recover_pct"])), r=PARAMS["inflation"])
+    Ad = synth_as_f64(A)
+    rng = np.random.default_rng(seed)
+    flops, ncols, t0 = 0, 0, time.perf_counter()
+    while time.perf_counter() - t0 < seconds:
+        cols = rng.choice(A.n, 2048, replace=False).astype(np.int32)
+        res = oracle.expand_cols(Ad, prm, cols=cols, kcap=PARAMS["select_k"])
+        flops += int(res.flops.sum())
+        ncols += len(cols)
+    dt = time.perf_counter() - t0
+    return 2.0 * flops / dt / 1e9, dt, ncols, oracle.num_threads()
+
+
+def synth_as_f64(A):
+    from paper_2002_10083_gb300 import synth
+    return synth.CSC(n=A.n, colptr=A.colptr, rowidx=A.rowidx, val=A.val.astype(np.float64))
+
+
+def run_reference(args):
+    rank, _, world = _env_rank()
+    if rank != 0:
+        return 0
+    A = make_workload(args.workload)
+    per_step = float(os.environ.get("MCL_REF_STEP_SECONDS", "6"))
+    vals = []
+    for i in range(args.warmup + args.steps):
+        g, dt, ncols, cores = oracle_gflops(A, per_step, seed=100 + i)
+        if i >= args.warmup:
+            vals.append((g, dt, ncols))
+    v = statistics.median([x[0] for x in vals])
+    ms = statistics.median([x[1] / x[2] * A.n * 1000.0 for x in vals])  # extrapolated full step
+    line = {"impl": "reference", "metric": METRIC, "value": round(v, 4), "unit": "GFLOP/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(ms, 1), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n": A.n, "nnz": A.nnz,
+                       "sample": f"{vals[0][2]} random columns per step (~{per_step:.0f} s of CPU work)"},
+            "cpu_baseline": {"value": round(v, 4), "unit": "GFLOP/s", "cores": cores, "kind": "oracle",
+                             "sample": f"random column samples, ~{per_step:.0f} s per step"},
+            "e2e": {"value": round(v, 4), "unit": "GFLOP/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_gpu(args):
+    import torch
+    rank, local, world = _env_rank()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist_
+        dist = dist_
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    from paper_2002_10083_gb300 import mcl
+    dev = local
+    torch.cuda.set_device(dev)
+    A = make_workload(args.workload)
+    n, nnz = A.n, A.nnz
+    D = mcl.DeviceCSC.from_host(A, device=f"cuda:{dev}")
+    ctx = mcl.Context(dev)
+    if args.sizing is not None:
+        ctx.set_option(mcl.OPT_SIZING, {"exact": 0, "flops": 1}[args.sizing])
+    prm = mcl.Params(**PARAMS)
+    stream = torch.cuda.current_stream()
+
+    # warm-up
+    for _ in range(args.warmup):
+        out, ch = ctx.expand(D, prm)
+        del out
+    torch.cuda.synchronize()
+    st = ctx.stats()
+    flops = int(st["flops"])
+
+    # timed region: device-resident inputs (A is ~400 MB, larger than L2)
+    gpu_idx = os.environ.get("CUDA_VISIBLE_DEVICES", str(dev)).split(",")[dev if world == 1 else local]
+    clk = ClockSampler(gpu_idx) if rank == 0 else None
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    if clk:
+        clk.start()
+        time.sleep(0.3)
+    l0 = mcl.launch_count()
+    ms_num, nnz_out, nnz_b, ms_tot = [], 0, 0, []
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        out, ch = ctx.expand(D, prm)
+        s = ctx.stats()
+        ms_num.append(s["ms_numeric"])
+        ms_tot.append(s["ms_total"])
+        nnz_out, nnz_b = int(s["nnz_out"]), int(s["nnz_b"])
+        del out
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    launches = mcl.launch_count() - l0
+    clocks = clk.stop() if clk else None
+    ms = e0.elapsed_time(e1) / args.steps
+    if dist:
+        t = torch.tensor([ms], device=f"cuda:{dev}")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+
+    # end to end through the C ABI with host buffers (pinned): H2D of A,
+    # the iteration, D2H of the resulting matrix
+    hcp = torch.from_numpy(A.colptr).pin_memory()
+    hri = torch.from_numpy(A.rowidx).pin_memory()
+    hva = torch.from_numpy(A.val.astype(np.float32)).pin_memory()
+    e2e_steps = max(1, min(args.steps, 3))
+    out_bytes = 0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        Dh = mcl.DeviceCSC(n, hcp.to(f"cuda:{dev}", non_blocking=True),
+                           hri.to(f"cuda:{dev}", non_blocking=True),
+                           hva.to(f"cuda:{dev}", non_blocking=True))
+        out, ch = ctx.expand(Dh, prm)
+        ocp = torch.empty(out.colptr.shape, dtype=torch.int64, pin_memory=True)
+        ori = torch.empty(out.rowidx.shape, dtype=torch.int32, pin_memory=True)
+        ova = torch.empty(out.val.shape, dtype=torch.float32, pin_memory=True)
+        ocp.copy_(out.colptr, non_blocking=True)
+        ori.copy_(out.rowidx, non_blocking=True)
+        ova.copy_(out.val, non_blocking=True)
+        torch.cuda.synchronize()
+        out_bytes = ocp.numel() * 8 + ori.numel() * 4 + ova.numel() * 4
+        del out, Dh
+    e2e_ms = (time.perf_counter() - t0) * 1000.0 / e2e_steps
+    in_bytes = hcp.numel() * 8 + hri.numel() * 4 + hva.numel() * 4
+
+    if rank != 0:
+        return 0
+    gflops = 2.0 * flops / (ms / 1000.0) / 1e9 * world
+    e2e_gflops = 2.0 * flops / (e2e_ms / 1000.0) / 1e9 * world
+    peak, peak_kind = _peaks()
+    t_num = statistics.median(ms_num)
+    b_alg = 8 * nnz + 8 * flops + 8 * nnz_out + 16 * n
+    achieved = b_alg / (t_num / 1000.0) / 1e9
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        g, dt, ncols, cores = oracle_gflops(A, args.cpu_seconds)
+        cpu = {"value": round(g, 4), "unit": "GFLOP/s", "cores": cores, "kind": "oracle",
+               "sample": f"{ncols} random columns of the same workload ({dt:.1f} s)"}
+    line = {
+        "metric": METRIC, "value": round(gflops, 2), "unit": "GFLOP/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": n, "nnz": nnz, "flops_per_step": flops,
+                   "nnz_b": nnz_b, "nnz_out": nnz_out,
+                   "form": args.sizing or "plain (exact symbolic sizing)",
+                   "l2": "inputs larger than L2 (A is %.0f MB)" % (in_bytes / 1e6),
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "iters_per_s": round(world * 1000.0 / ms, 3),
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                     "frac": round(achieved / peak, 4), "traffic": None,
+                     "kernel": "k_numeric (all accumulator configurations of one step)",
+                     "algorithmic_bytes": b_alg, "kernel_ms": round(t_num, 3),
+                     "peak_kind": peak_kind},
+        "cpu_baseline": cpu,
+        "e2e": {"value": round(e2e_gflops, 2), "unit": "GFLOP/s", "h2d_bytes_per_step": in_bytes,
+                "d2h_bytes_per_step": out_bytes, "ms_per_step": round(e2e_ms, 3)},
+        "gpu_launches": int(launches),
+        "clocks": clocks,
+        "stage_ms": {k: round(v, 3) for k, v in ctx.stats().items() if k.startswith("ms_")},
+    }
+    print(json.dumps(line), flush=True)
+    ctx.close()
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="zipf1m")
+    ap.add_argument("--sizing", default=None, choices=[None, "exact", "flops"])
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

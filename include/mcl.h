@@ -1,0 +1,226 @@
+/*
+ * mcl.h -- C ABI of the GB300 (sm_103a) Markov Cluster expansion library.
+ *
+ * One MCL iteration (Algorithm 1 of Selvitopi, Hussain, Azad, Buluc,
+ * "Optimizing High Performance Markov Clustering for Pre-Exascale
+ * Architectures"): expansion B = A A (Alg. 1, expansion, "random walks from
+ * all vertices performed as SpGEMM"), Prune (Alg. 1, Prune: drop entries
+ * below a threshold and keep the top k of every column; recovery to a mass
+ * fraction is this library's reading, below), inflation (Alg. 1, Hadamard
+ * power) followed by column renormalisation, and the chaos measure used for
+ * the loop's convergence test (Alg. 1, "while change in successive
+ * iterations").  Clusters are the connected components of the final
+ * matrix (Alg. 1, return).
+ *
+ * Matrices are square n x n in CSC (Section III-B: CSC is CSR of the
+ * transpose, so column-wise products need no conversion):
+ *   colptr  int64[n+1], nondecreasing, colptr[0] == 0, colptr[n] == nnz
+ *   rowidx  int32[nnz], strictly increasing inside each column, in [0, n)
+ *   val     float[nnz], finite and >= 0 (FP32)
+ * Every array pointer in mcl_csc is DEVICE memory of the context's device.
+ *
+ * Prune rule (per column j of B, s = sum_i b_ij, entries ranked by value
+ * descending, equal values by row ascending):
+ *   t     = #{ i : b_ij >= threshold }
+ *   m_rec = smallest m whose top-m mass reaches recover_pct * s
+ *   m*    = min(K_rec, max(min(t, select_k), m_rec)),  K_rec = recover_k or select_k
+ *   keep the top m* entries.
+ * Inflation: a_ij = b_ij^r / sum_i b_ij^r over the kept entries (FP32 power,
+ * FP64 column sum).  chaos_j = max(0, max_i a_ij - sum_i a_ij^2) in FP64;
+ * chaos = max_j chaos_j.
+ *
+ * Precision: FP32 values and FP32 accumulation of the products; FP64 only
+ * in the column sums and the chaos reduction.
+ *
+ * Ownership: the caller owns all inputs.  Outputs written into an mcl_csc
+ * are allocated by the library with the context's allocator (see
+ * mcl_create) and belong to the caller, who releases them with the matching
+ * free.  Scratch space is owned by the context and reused across calls.
+ *
+ * Errors: every call returns an mcl_status; nothing is thrown across the
+ * ABI.  After an error the context stays usable and mcl_last_error returns
+ * a message.  Streams: every call is ordered on the given cudaStream_t
+ * (passed as void*, NULL = legacy default stream).  Calls that must size an
+ * output or return a host value synchronise that stream (noted per call).
+ * A context must not be used by two host threads at once.
+ */
+#ifndef MCL_H_
+#define MCL_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    MCL_OK = 0,
+    MCL_ERR_INVALID = 1,        /* bad argument or malformed CSC */
+    MCL_ERR_OOM = 2,            /* allocator returned NULL */
+    MCL_ERR_CUDA = 3,           /* a CUDA runtime call failed */
+    MCL_ERR_TIMEOUT = 4,        /* a bounded device wait gave up */
+    MCL_ERR_NOT_CONVERGED = 5,  /* mcl_run hit max_iters with chaos >= eps */
+    MCL_ERR_INTERNAL = 6        /* a device-side consistency check failed */
+} mcl_status;
+
+typedef struct mcl_ctx mcl_ctx;
+
+typedef struct {
+    int32_t n;        /* rows == columns, 0 <= n <= 2^31 - 2 */
+    int64_t nnz;      /* == colptr[n] */
+    int64_t* colptr;  /* device int64[n+1] */
+    int32_t* rowidx;  /* device int32[nnz] */
+    float* val;       /* device float[nnz] */
+} mcl_csc;
+
+typedef struct {
+    float threshold;      /* prune threshold theta (b >= theta survives) */
+    int32_t select_k;     /* K: top-k kept per column, 1 <= K <= MCL_MAX_SELECT_K */
+    float recover_pct;    /* p in [0, 1]: recovery mass fraction */
+    int32_t recover_k;    /* K_rec cap on recovery; <= 0 means K */
+    float inflation;      /* r > 0 (r = 2 in all of the paper's runs) */
+    double chaos_eps;     /* mcl_run stops when chaos < chaos_eps */
+    int32_t max_iters;    /* mcl_run iteration cap */
+    int32_t use_estimator;/* 0: exact symbolic sizing; 1: learned estimator */
+    int32_t batched;      /* mcl_run with comp_offsets: per-component stop */
+} mcl_params;
+
+#define MCL_MAX_SELECT_K 4096
+
+/* Device allocator used for outputs and scratch: returns device memory of
+ * at least `bytes` (256-byte aligned) or NULL; `stream` is the call's
+ * stream.  NULL callbacks mean cudaMallocAsync / cudaFreeAsync. */
+typedef void* (*mcl_alloc_fn)(size_t bytes, void* user, void* stream);
+typedef void (*mcl_free_fn)(void* ptr, void* user, void* stream);
+
+/* Per-call statistics of the last mcl_expand (or last mcl_run iteration). */
+typedef struct {
+    int64_t flops;            /* sum_j flops_j (multiply-adds), Section II notation */
+    int64_t nnz_in;           /* nnz(A) */
+    int64_t nnz_b;            /* nnz(A A) before pruning (exact, counted in the numeric pass) */
+    int64_t nnz_out;          /* nnz after prune */
+    int64_t estimator_misses; /* columns whose nnz exceeded the size estimate */
+    int64_t range_splits;     /* accumulator overflows resolved by narrowing the row range */
+    double chaos;             /* max_j chaos_j */
+    float ms_colstats, ms_estimate, ms_bin, ms_numeric, ms_compact, ms_chaos, ms_total;
+    int32_t bins_used;
+    int32_t iterations;
+} mcl_stats;
+
+/* Create a context on `device` (made current by every call).  alloc/free
+ * may be NULL (see mcl_alloc_fn).  Returns MCL_ERR_INVALID for a bad device. */
+mcl_status mcl_create(mcl_ctx** ctx, int device, mcl_alloc_fn alloc, mcl_free_fn release,
+                      void* alloc_user);
+
+/* Release the context and its scratch (synchronises the device). */
+void mcl_destroy(mcl_ctx* ctx);
+
+/* Message for the last failed call on ctx (static storage inside ctx). */
+const char* mcl_last_error(mcl_ctx* ctx);
+
+/* Library version string. */
+const char* mcl_version(void);
+
+/* Number of CUDA kernels this library has launched in this process, over
+ * all contexts (for accounting; not synchronised with the device). */
+int64_t mcl_launch_count(void);
+
+/*
+ * One fused MCL iteration: expansion B = A A, prune (threshold / top-k /
+ * recovery), inflation and renormalisation, per-column chaos (Alg. 1,
+ * expansion + Prune + inflation; the per-column fusion of expansion and
+ * pruning follows Section II, "HipMCL fuses expansion and pruning").  The
+ * unpruned B is never materialised.  A must be square; it need not be
+ * column stochastic (the prune rule uses each column's own sum).
+ * out: filled with a new CSC allocated by the context allocator (rows
+ * sorted).  chaos: optional host pointer receiving max_j chaos_j.
+ * Synchronises `stream` (to size the output).
+ */
+mcl_status mcl_expand(mcl_ctx* ctx, const mcl_csc* A, const mcl_params* prm, mcl_csc* out,
+                      double* chaos, void* stream);
+
+/*
+ * The prune rule alone (Alg. 1, Prune, with the recovery reading above) on
+ * an already materialised matrix B (square CSC): kept entries keep their B
+ * values (no renormalisation).  out allocated as in mcl_expand.
+ * Synchronises `stream`.
+ */
+mcl_status mcl_prune_select_recover(mcl_ctx* ctx, const mcl_csc* B, const mcl_params* prm,
+                                    mcl_csc* out, void* stream);
+
+/*
+ * Inflation (Alg. 1, Hadamard power r) and column renormalisation, in
+ * place on A's values: a_ij <- a_ij^r / sum_i a_ij^r (FP64 sum).  Columns
+ * whose powers sum to 0 become 0.  Does not synchronise.
+ */
+mcl_status mcl_inflate_normalize(mcl_ctx* ctx, mcl_csc* A, float r, void* stream);
+
+/*
+ * chaos = max_j max(0, max_i a_ij - sum_i a_ij^2), FP64, written to the
+ * host pointer `chaos` (the convergence measure for Alg. 1's loop test).
+ * chaos_cols: optional device double[n] receiving chaos_j.
+ * Synchronises `stream`.
+ */
+mcl_status mcl_chaos(mcl_ctx* ctx, const mcl_csc* A, double* chaos, double* chaos_cols,
+                     void* stream);
+
+/*
+ * Connected components of the undirected pattern of A (Alg. 1, return):
+ * labels (device int32[n]) receive the smallest vertex id of each vertex's
+ * component.  Does not synchronise.
+ */
+mcl_status mcl_components(mcl_ctx* ctx, const mcl_csc* A, int32_t* labels, void* stream);
+
+/*
+ * Algorithm 1 to convergence: iterate mcl_expand until chaos < chaos_eps
+ * or max_iters, then label clusters.  comp_offsets (HOST int32[ncomp+1],
+ * or NULL) splits a block-diagonal A into independent components; with
+ * prm->batched != 0 each component stops on its own chaos and its columns
+ * are carried unchanged afterwards, while all still-active columns of all
+ * components are expanded together in one pass per iteration.
+ * labels: device int32[n].  iters: host, receives the iteration count (the
+ * maximum over components).  chaos_hist: host double[max_iters] or NULL.
+ * final_out: optional; receives the final matrix (allocated as in
+ * mcl_expand).  Synchronises `stream` every iteration.  Returns
+ * MCL_ERR_NOT_CONVERGED (with all outputs valid) when max_iters is reached.
+ */
+mcl_status mcl_run(mcl_ctx* ctx, const mcl_csc* A0, const int32_t* comp_offsets, int32_t ncomp,
+                   const mcl_params* prm, int32_t* labels, int32_t* iters, double* chaos_hist,
+                   mcl_csc* final_out, void* stream);
+
+/*
+ * Exact symbolic expansion: flops_j = sum_{k in inds(A_*j)} nnz(A_*k) and
+ * nnz_j = nnz((A A)_*j) for every column (Section II notation; the exact
+ * memory estimate of Sections II and V, "symbolic SpGEMM").  flops and nnz_out are
+ * device int64[n] (either may be NULL).  Does not synchronise.
+ */
+mcl_status mcl_symbolic(mcl_ctx* ctx, const mcl_csc* A, int64_t* flops, int64_t* nnz_out,
+                        void* stream);
+
+/*
+ * Tuning options of a context (not part of the method):
+ *   1 MCL_OPT_SIZING     -1 follow prm->use_estimator (default), 0 exact
+ *                        symbolic pass, 1 the flops bound min(flops_j, span_j)
+ *   2 MCL_OPT_CONF_MASK  bit mask of accumulator configurations (bit 2 or 3
+ *                        must stay set)
+ *   3 MCL_OPT_VALIDATE   1 (default) validate inputs
+ *   4 MCL_OPT_EST_SCALE  multiply every size estimate by value/1000 (1000 =
+ *                        unchanged); a deliberate mis-estimate exercises the
+ *                        accumulator overflow path (results stay exact)
+ * Returns MCL_ERR_INVALID for an unknown option or value.
+ */
+#define MCL_OPT_SIZING 1
+#define MCL_OPT_CONF_MASK 2
+#define MCL_OPT_VALIDATE 3
+#define MCL_OPT_EST_SCALE 4
+mcl_status mcl_set_option(mcl_ctx* ctx, int option, int64_t value);
+
+/* Statistics of the last mcl_expand / mcl_run on ctx. */
+mcl_status mcl_get_stats(mcl_ctx* ctx, mcl_stats* stats);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MCL_H_ */

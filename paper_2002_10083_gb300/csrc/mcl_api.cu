@@ -1,0 +1,606 @@
+// C ABI of the MCL expansion library: context, scratch, argument checks and
+// the host-side order of the kernels of one iteration (see mcl.h).
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "mcl.h"
+#include "mcl_internal.h"
+
+using namespace mcl;
+
+namespace {
+
+struct Buf {
+    void* p = nullptr;
+    size_t bytes = 0;
+};
+
+}  // namespace
+
+struct mcl_ctx {
+    int device = 0;
+    int num_sms = 0;
+    mcl_alloc_fn alloc = nullptr;
+    mcl_free_fn release = nullptr;
+    void* user = nullptr;
+    char err[512] = {0};
+    // scratch
+    Buf flops, rlo, rhi, cap, off, est, bucket, work, kept, chaos, bnnz, tmp_row, tmp_val,
+        cursors, scan, ctr, active;
+    DevCounters* hctr = nullptr;  // pinned host mirror
+    mcl_stats stats{};
+    cudaEvent_t ev[8] = {};
+    // options
+    int sizing = -1;        // -1: from params (exact or learned); 0 exact; 1 flops bound
+    int conf_mask = 0xF;    // accumulator configurations allowed
+    int validate = 1;
+    int est_milli = 1000;   // estimate scale (test knob)
+    // learned estimator (weights on device)
+    Buf mlp_w;
+    int has_estimator = 0;
+    float est_safety = 1.25f;
+    Buf feats, pred;
+};
+
+namespace {
+
+mcl_status fail(mcl_ctx* c, mcl_status st, const char* fmt, ...) {
+    if (c) {
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(c->err, sizeof(c->err), fmt, ap);
+        va_end(ap);
+    }
+    return st;
+}
+
+void* dev_alloc(mcl_ctx* c, size_t bytes, cudaStream_t s) {
+    if (bytes == 0) bytes = 256;
+    bytes = (bytes + 255) & ~(size_t)255;
+    if (c->alloc) return c->alloc(bytes, c->user, (void*)s);
+    void* p = nullptr;
+    if (cudaMallocAsync(&p, bytes, s) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return p;
+}
+
+void dev_free(mcl_ctx* c, void* p, cudaStream_t s) {
+    if (!p) return;
+    if (c->release)
+        c->release(p, c->user, (void*)s);
+    else
+        cudaFreeAsync(p, s);
+}
+
+bool ensure(mcl_ctx* c, Buf& b, size_t bytes, cudaStream_t s) {
+    if (b.p && b.bytes >= bytes) return true;
+    dev_free(c, b.p, s);
+    size_t nb = bytes + bytes / 8 + 256;
+    b.p = dev_alloc(c, nb, s);
+    b.bytes = b.p ? nb : 0;
+    return b.p != nullptr;
+}
+
+#define CUDA_TRY(ctx, call)                                                              \
+    do {                                                                                 \
+        cudaError_t e_ = (call);                                                         \
+        if (e_ != cudaSuccess)                                                           \
+            return fail(ctx, MCL_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_));   \
+    } while (0)
+
+mcl_status check_launch(mcl_ctx* c, const char* what) {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(c, MCL_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+    return MCL_OK;
+}
+
+mcl_status err_flags(mcl_ctx* c, unsigned f) {
+    if (!f) return MCL_OK;
+    if (f & (ERR_COLPTR | ERR_ROW_RANGE | ERR_ROW_ORDER | ERR_VALUE))
+        return fail(c, MCL_ERR_INVALID, "malformed CSC input (flags 0x%x: %s%s%s%s)", f,
+                    (f & ERR_COLPTR) ? "colptr " : "", (f & ERR_ROW_RANGE) ? "row-range " : "",
+                    (f & ERR_ROW_ORDER) ? "row-order " : "", (f & ERR_VALUE) ? "value " : "");
+    if (f & ERR_TIMEOUT) return fail(c, MCL_ERR_TIMEOUT, "a bounded device loop gave up");
+    return fail(c, MCL_ERR_INTERNAL, "device consistency check failed (flags 0x%x)", f);
+}
+
+mcl_status check_params(mcl_ctx* c, const mcl_params* prm, PruneParams* pp, bool need_inflation) {
+    if (!prm) return fail(c, MCL_ERR_INVALID, "params is NULL");
+    if (prm->select_k < 1 || prm->select_k > MCL_MAX_SELECT_K)
+        return fail(c, MCL_ERR_INVALID, "select_k must be in [1, %d]", MCL_MAX_SELECT_K);
+    int krec = prm->recover_k > 0 ? prm->recover_k : prm->select_k;
+    if (krec > MCL_MAX_SELECT_K)
+        return fail(c, MCL_ERR_INVALID, "recover_k must be <= %d", MCL_MAX_SELECT_K);
+    if (!(prm->recover_pct >= 0.0f && prm->recover_pct <= 1.0f))
+        return fail(c, MCL_ERR_INVALID, "recover_pct must be in [0, 1]");
+    if (!(prm->threshold >= 0.0f) || !(prm->threshold <= 3.0e38f))
+        return fail(c, MCL_ERR_INVALID, "threshold must be finite and >= 0");
+    if (need_inflation && !(prm->inflation > 0.0f && prm->inflation <= 1.0e6f))
+        return fail(c, MCL_ERR_INVALID, "inflation must be > 0");
+    pp->theta = prm->threshold;
+    pp->K = prm->select_k;
+    pp->p = prm->recover_pct;
+    pp->Krec = krec;
+    pp->ksel = prm->select_k > krec ? prm->select_k : krec;
+    pp->r = prm->inflation;
+    pp->inflate = 1;
+    return MCL_OK;
+}
+
+mcl_status check_csc(mcl_ctx* c, const mcl_csc* A, const char* name) {
+    if (!A) return fail(c, MCL_ERR_INVALID, "%s is NULL", name);
+    if (A->n < 0 || A->n > 0x7FFFFFFE) return fail(c, MCL_ERR_INVALID, "%s: bad n", name);
+    if (A->nnz < 0) return fail(c, MCL_ERR_INVALID, "%s: bad nnz", name);
+    if (!A->colptr) return fail(c, MCL_ERR_INVALID, "%s: colptr is NULL", name);
+    if (A->nnz > 0 && (!A->rowidx || !A->val))
+        return fail(c, MCL_ERR_INVALID, "%s: rowidx/val is NULL", name);
+    return MCL_OK;
+}
+
+CscView view(const mcl_csc* A) {
+    return CscView{A->n, A->nnz, A->colptr, A->rowidx, A->val};
+}
+
+ExpandBuffers buffers(mcl_ctx* c) {
+    ExpandBuffers b{};
+    b.flops = (int64_t*)c->flops.p;
+    b.rlo = (int32_t*)c->rlo.p;
+    b.rhi = (int32_t*)c->rhi.p;
+    b.cap = (int64_t*)c->cap.p;
+    b.off = (int64_t*)c->off.p;
+    b.est = (int64_t*)c->est.p;
+    b.bucket = (int32_t*)c->bucket.p;
+    b.work = (int32_t*)c->work.p;
+    b.kept = (int32_t*)c->kept.p;
+    b.chaos = (double*)c->chaos.p;
+    b.bnnz = (int64_t*)c->bnnz.p;
+    b.tmp_row = (int32_t*)c->tmp_row.p;
+    b.tmp_val = (float*)c->tmp_val.p;
+    b.cursors = (int32_t*)c->cursors.p;
+    b.cur_stride = 0;
+    b.scan_tmp = (int64_t*)c->scan.p;
+    b.ctr = (DevCounters*)c->ctr.p;
+    b.active = nullptr;
+    return b;
+}
+
+mcl_status ensure_columns(mcl_ctx* c, int64_t n, cudaStream_t s) {
+    const size_t n1 = (size_t)n + 1;
+    bool ok = ensure(c, c->flops, n1 * 8, s) && ensure(c, c->rlo, n1 * 4, s) &&
+              ensure(c, c->rhi, n1 * 4, s) && ensure(c, c->cap, n1 * 8, s) &&
+              ensure(c, c->off, n1 * 8, s) && ensure(c, c->est, n1 * 8, s) &&
+              ensure(c, c->bucket, n1 * 4, s) && ensure(c, c->work, n1 * 4, s) &&
+              ensure(c, c->kept, n1 * 4, s) && ensure(c, c->chaos, n1 * 8, s) &&
+              ensure(c, c->bnnz, n1 * 8, s) &&
+              ensure(c, c->scan, (size_t)scan_tmp_len_for(n1) * 8, s) &&
+              ensure(c, c->ctr, sizeof(DevCounters), s);
+    if (!ok) return fail(c, MCL_ERR_OOM, "scratch allocation failed (n=%lld)", (long long)n);
+    return MCL_OK;
+}
+
+mcl_status read_counters(mcl_ctx* c, cudaStream_t s) {
+    CUDA_TRY(c, cudaMemcpyAsync(c->hctr, c->ctr.p, sizeof(DevCounters), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(c, cudaStreamSynchronize(s));
+    return MCL_OK;
+}
+
+double chaos_from_bits(unsigned long long b) {
+    double d;
+    memcpy(&d, &b, 8);
+    return d;
+}
+
+int max_numeric_grid(mcl_ctx* c, int ksel) {
+    int g = 0;
+    for (int q = 0; q < NCONF; ++q) {
+        if (!conf_allowed(q, ksel)) continue;
+        int gq = numeric_grid(q, ksel, c->num_sms);
+        if (gq > g) g = gq;
+    }
+    int gs = symbolic_grid(c->num_sms);
+    return g > gs ? g : gs;
+}
+
+}  // namespace
+
+// Learned-estimator hook (mcl_estimator.cu): fills b.est from features and
+// the MLP; returns MCL_OK or an error.
+mcl_status mcl_internal_estimate(mcl_ctx* c, const mcl_csc* A, const ExpandBuffers& b,
+                                 cudaStream_t s);
+
+extern "C" {
+
+const char* mcl_version(void) { return "mcl-gb300 1.0 (sm_103a)"; }
+
+int64_t mcl_launch_count(void) { return (int64_t)launches_total(); }
+
+mcl_status mcl_create(mcl_ctx** out, int device, mcl_alloc_fn alloc, mcl_free_fn release,
+                      void* alloc_user) {
+    if (!out) return MCL_ERR_INVALID;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+        cudaGetLastError();
+        return MCL_ERR_INVALID;
+    }
+    if ((alloc == nullptr) != (release == nullptr)) return MCL_ERR_INVALID;
+    mcl_ctx* c = new mcl_ctx();
+    c->device = device;
+    c->alloc = alloc;
+    c->release = release;
+    c->user = alloc_user;
+    if (cudaSetDevice(device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
+        cudaMallocHost((void**)&c->hctr, sizeof(DevCounters)) != cudaSuccess) {
+        cudaGetLastError();
+        delete c;
+        return MCL_ERR_CUDA;
+    }
+    for (auto& e : c->ev) cudaEventCreate(&e);
+    *out = c;
+    return MCL_OK;
+}
+
+void mcl_destroy(mcl_ctx* c) {
+    if (!c) return;
+    cudaSetDevice(c->device);
+    cudaDeviceSynchronize();
+    Buf* all[] = {&c->flops, &c->rlo,     &c->rhi,     &c->cap,     &c->off,  &c->est,
+                  &c->bucket, &c->work,   &c->kept,    &c->chaos,   &c->bnnz, &c->tmp_row,
+                  &c->tmp_val, &c->cursors, &c->scan,  &c->ctr,     &c->active, &c->mlp_w,
+                  &c->feats,  &c->pred};
+    for (Buf* b : all) dev_free(c, b->p, 0);
+    cudaDeviceSynchronize();
+    for (auto& e : c->ev) cudaEventDestroy(e);
+    if (c->hctr) cudaFreeHost(c->hctr);
+    delete c;
+}
+
+const char* mcl_last_error(mcl_ctx* c) { return c ? c->err : "null context"; }
+
+mcl_status mcl_get_stats(mcl_ctx* c, mcl_stats* st) {
+    if (!c || !st) return MCL_ERR_INVALID;
+    *st = c->stats;
+    return MCL_OK;
+}
+
+mcl_status mcl_set_option(mcl_ctx* c, int option, int64_t value) {
+    if (!c) return MCL_ERR_INVALID;
+    switch (option) {
+        case 1:  // sizing: -1 from params, 0 exact symbolic, 1 flops bound
+            if (value < -1 || value > 1) return fail(c, MCL_ERR_INVALID, "bad sizing option");
+            c->sizing = (int)value;
+            return MCL_OK;
+        case 2:  // accumulator configuration mask
+            if ((value & 0xC) == 0) return fail(c, MCL_ERR_INVALID, "conf mask must keep conf 2 or 3");
+            c->conf_mask = (int)(value & 0xF);
+            return MCL_OK;
+        case 3:
+            c->validate = value != 0;
+            return MCL_OK;
+        case 4:  // estimate scale in thousandths (1000 = as estimated)
+            if (value < 1 || value > 1000000) return fail(c, MCL_ERR_INVALID, "bad scale");
+            c->est_milli = (int)value;
+            return MCL_OK;
+        default:
+            return fail(c, MCL_ERR_INVALID, "unknown option %d", option);
+    }
+}
+
+// One fused iteration on the given stream.  `active` (device uint8[n] or
+// NULL) marks the columns to expand; inactive columns are copied through.
+static mcl_status expand_impl(mcl_ctx* c, const mcl_csc* A, const mcl_params* prm, mcl_csc* out,
+                              double* chaos, cudaStream_t s, const uint8_t* active) {
+    PruneParams pp;
+    mcl_status st = check_params(c, prm, &pp, true);
+    if (st) return st;
+    if ((st = check_csc(c, A, "A"))) return st;
+    if (!out) return fail(c, MCL_ERR_INVALID, "out is NULL");
+    CUDA_TRY(c, cudaSetDevice(c->device));
+    const int64_t n = A->n;
+    if ((st = ensure_columns(c, n, s))) return st;
+    ExpandBuffers b = buffers(c);
+    b.active = active;
+    const CscView Av = view(A);
+    cudaEventRecord(c->ev[0], s);
+    CUDA_TRY(c, cudaMemsetAsync(c->ctr.p, 0, sizeof(DevCounters), s));
+    launch_colstats(Av, pp, b, c->num_sms, s);
+    launch_exclusive_scan<int64_t>(b.cap, n, b.off, b.scan_tmp, &b.ctr->cap_total, s);
+    if ((st = check_launch(c, "colstats"))) return st;
+    cudaEventRecord(c->ev[1], s);
+    if ((st = read_counters(c, s))) return st;
+    if ((st = err_flags(c, c->hctr->err))) return st;
+    const int64_t cap_total = (int64_t)c->hctr->cap_total;
+    const int max_deg = c->hctr->max_deg;
+    b.cur_stride = (max_deg + 31) & ~31;
+    if (b.cur_stride < 32) b.cur_stride = 32;
+    const int grid_max = max_numeric_grid(c, pp.ksel);
+    if (!ensure(c, c->tmp_row, (size_t)cap_total * 4 + 4, s) ||
+        !ensure(c, c->tmp_val, (size_t)cap_total * 4 + 4, s) ||
+        !ensure(c, c->cursors, (size_t)grid_max * 2 * b.cur_stride * 4, s))
+        return fail(c, MCL_ERR_OOM, "scratch allocation failed (capacity %lld)",
+                    (long long)cap_total);
+    b.tmp_row = (int32_t*)c->tmp_row.p;
+    b.tmp_val = (float*)c->tmp_val.p;
+    b.cursors = (int32_t*)c->cursors.p;
+    // ---- size estimate ----
+    const int sizing = c->sizing >= 0 ? c->sizing : (prm->use_estimator ? 2 : 0);
+    if (sizing == 2) {
+        if (!c->has_estimator)
+            return fail(c, MCL_ERR_INVALID, "use_estimator set but no estimator loaded");
+        if ((st = mcl_internal_estimate(c, A, b, s))) return st;
+    } else if (sizing == 1) {
+        launch_est_from_flops(Av, b, s);
+    } else {
+        launch_symbolic(Av, b, b.est, c->num_sms, grid_max, s);
+    }
+    if (c->est_milli != 1000) launch_scale_est(A->n, b.est, c->est_milli, s);
+    if ((st = check_launch(c, "estimate"))) return st;
+    cudaEventRecord(c->ev[2], s);
+    // ---- binning + numeric ----
+    launch_binning(Av, pp, b, c->conf_mask, s);
+    cudaEventRecord(c->ev[3], s);
+    int used = 0;
+    for (int q = NCONF - 1; q >= 0; --q) {
+        if (!conf_allowed(q, pp.ksel) || !((c->conf_mask >> q) & 1)) continue;
+        int g = numeric_grid(q, pp.ksel, c->num_sms);
+        launch_numeric(q, Av, pp, b, g, s);
+        ++used;
+    }
+    if ((st = check_launch(c, "numeric"))) return st;
+    cudaEventRecord(c->ev[4], s);
+    launch_finalize_stats(A->n, b, s);
+    // ---- output ----
+    int64_t* colptr_out = (int64_t*)dev_alloc(c, (size_t)(n + 1) * 8, s);
+    if (!colptr_out) return fail(c, MCL_ERR_OOM, "output colptr allocation failed");
+    if (active) {
+        // inactive columns keep their input length
+        return fail(c, MCL_ERR_INTERNAL, "active mask requires mcl_run");
+    }
+    launch_exclusive_scan<int32_t>(b.kept, n, colptr_out, b.scan_tmp, &b.ctr->nnz_out, s);
+    if ((st = check_launch(c, "scan"))) {
+        dev_free(c, colptr_out, s);
+        return st;
+    }
+    cudaEventRecord(c->ev[5], s);
+    if ((st = read_counters(c, s)) || (st = err_flags(c, c->hctr->err))) {
+        dev_free(c, colptr_out, s);
+        return st;
+    }
+    const int64_t nnz_out = (int64_t)c->hctr->nnz_out;
+    int32_t* row_out = (int32_t*)dev_alloc(c, (size_t)nnz_out * 4 + 4, s);
+    float* val_out = (float*)dev_alloc(c, (size_t)nnz_out * 4 + 4, s);
+    if (!row_out || !val_out) {
+        dev_free(c, colptr_out, s);
+        dev_free(c, row_out, s);
+        dev_free(c, val_out, s);
+        return fail(c, MCL_ERR_OOM, "output allocation failed (nnz %lld)", (long long)nnz_out);
+    }
+    launch_compact(Av, b, colptr_out, row_out, val_out, s);
+    if ((st = check_launch(c, "compact"))) return st;
+    cudaEventRecord(c->ev[6], s);
+    out->n = A->n;
+    out->nnz = nnz_out;
+    out->colptr = colptr_out;
+    out->rowidx = row_out;
+    out->val = val_out;
+    const double ch = chaos_from_bits(c->hctr->chaos_bits);
+    if (chaos) *chaos = ch;
+    // statistics (elapsed times up to the last synchronisation)
+    mcl_stats& S = c->stats;
+    S.flops = (int64_t)c->hctr->flops;
+    S.nnz_in = A->nnz;
+    S.nnz_b = (int64_t)c->hctr->nnz_b;
+    S.nnz_out = nnz_out;
+    S.estimator_misses = (int64_t)c->hctr->misses;
+    S.range_splits = (int64_t)c->hctr->splits;
+    S.chaos = ch;
+    S.bins_used = used;
+    cudaEventElapsedTime(&S.ms_colstats, c->ev[0], c->ev[1]);
+    cudaEventElapsedTime(&S.ms_estimate, c->ev[1], c->ev[2]);
+    cudaEventElapsedTime(&S.ms_bin, c->ev[2], c->ev[3]);
+    cudaEventElapsedTime(&S.ms_numeric, c->ev[3], c->ev[4]);
+    cudaEventElapsedTime(&S.ms_chaos, c->ev[4], c->ev[5]);
+    cudaEventElapsedTime(&S.ms_total, c->ev[0], c->ev[5]);
+    S.ms_compact = 0.0f;
+    return MCL_OK;
+}
+
+mcl_status mcl_expand(mcl_ctx* c, const mcl_csc* A, const mcl_params* prm, mcl_csc* out,
+                      double* chaos, void* stream) {
+    if (!c) return MCL_ERR_INVALID;
+    return expand_impl(c, A, prm, out, chaos, (cudaStream_t)stream, nullptr);
+}
+
+mcl_status mcl_symbolic(mcl_ctx* c, const mcl_csc* A, int64_t* flops, int64_t* nnz_out,
+                        void* stream) {
+    if (!c) return MCL_ERR_INVALID;
+    mcl_status st;
+    if ((st = check_csc(c, A, "A"))) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    CUDA_TRY(c, cudaSetDevice(c->device));
+    const int64_t n = A->n;
+    if ((st = ensure_columns(c, n, s))) return st;
+    ExpandBuffers b = buffers(c);
+    const CscView Av = view(A);
+    PruneParams pp{};
+    pp.Krec = 1;
+    CUDA_TRY(c, cudaMemsetAsync(c->ctr.p, 0, sizeof(DevCounters), s));
+    launch_colstats(Av, pp, b, c->num_sms, s);
+    if ((st = read_counters(c, s))) return st;
+    if ((st = err_flags(c, c->hctr->err))) return st;
+    b.cur_stride = ((c->hctr->max_deg + 31) & ~31) + 32;
+    const int grid = symbolic_grid(c->num_sms);
+    if (!ensure(c, c->cursors, (size_t)grid * 2 * b.cur_stride * 4, s))
+        return fail(c, MCL_ERR_OOM, "cursor scratch allocation failed");
+    b.cursors = (int32_t*)c->cursors.p;
+    if (nnz_out) launch_symbolic(Av, b, nnz_out, c->num_sms, grid, s);
+    if (flops && n > 0)
+        CUDA_TRY(c, cudaMemcpyAsync(flops, b.flops, (size_t)n * 8, cudaMemcpyDeviceToDevice, s));
+    return check_launch(c, "symbolic");
+}
+
+mcl_status mcl_prune_select_recover(mcl_ctx* c, const mcl_csc* B, const mcl_params* prm,
+                                    mcl_csc* out, void* stream) {
+    if (!c) return MCL_ERR_INVALID;
+    PruneParams pp;
+    mcl_status st = check_params(c, prm, &pp, false);
+    if (st) return st;
+    pp.inflate = 0;
+    if ((st = check_csc(c, B, "B"))) return st;
+    if (!out) return fail(c, MCL_ERR_INVALID, "out is NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    CUDA_TRY(c, cudaSetDevice(c->device));
+    const int64_t n = B->n;
+    if ((st = ensure_columns(c, n, s))) return st;
+    ExpandBuffers b = buffers(c);
+    const CscView Bv = view(B);
+    CUDA_TRY(c, cudaMemsetAsync(c->ctr.p, 0, sizeof(DevCounters), s));
+    launch_colstats(Bv, pp, b, c->num_sms, s);  // validation
+    if ((st = read_counters(c, s))) return st;
+    if ((st = err_flags(c, c->hctr->err))) return st;
+    launch_prune_cap(Bv, pp.Krec, b, s);
+    launch_exclusive_scan<int64_t>(b.cap, n, b.off, b.scan_tmp, &b.ctr->cap_total, s);
+    if ((st = read_counters(c, s))) return st;
+    const int64_t cap_total = (int64_t)c->hctr->cap_total;
+    if (!ensure(c, c->tmp_row, (size_t)cap_total * 4 + 4, s) ||
+        !ensure(c, c->tmp_val, (size_t)cap_total * 4 + 4, s))
+        return fail(c, MCL_ERR_OOM, "scratch allocation failed");
+    b.tmp_row = (int32_t*)c->tmp_row.p;
+    b.tmp_val = (float*)c->tmp_val.p;
+    launch_prune(Bv, pp, b, c->num_sms, s);
+    if ((st = check_launch(c, "prune"))) return st;
+    int64_t* colptr_out = (int64_t*)dev_alloc(c, (size_t)(n + 1) * 8, s);
+    if (!colptr_out) return fail(c, MCL_ERR_OOM, "output colptr allocation failed");
+    launch_exclusive_scan<int32_t>(b.kept, n, colptr_out, b.scan_tmp, &b.ctr->nnz_out, s);
+    if ((st = read_counters(c, s)) || (st = err_flags(c, c->hctr->err))) {
+        dev_free(c, colptr_out, s);
+        return st;
+    }
+    const int64_t nnz_out = (int64_t)c->hctr->nnz_out;
+    int32_t* row_out = (int32_t*)dev_alloc(c, (size_t)nnz_out * 4 + 4, s);
+    float* val_out = (float*)dev_alloc(c, (size_t)nnz_out * 4 + 4, s);
+    if (!row_out || !val_out) {
+        dev_free(c, colptr_out, s);
+        dev_free(c, row_out, s);
+        dev_free(c, val_out, s);
+        return fail(c, MCL_ERR_OOM, "output allocation failed");
+    }
+    launch_compact(Bv, b, colptr_out, row_out, val_out, s);
+    if ((st = check_launch(c, "compact"))) return st;
+    out->n = B->n;
+    out->nnz = nnz_out;
+    out->colptr = colptr_out;
+    out->rowidx = row_out;
+    out->val = val_out;
+    return MCL_OK;
+}
+
+mcl_status mcl_inflate_normalize(mcl_ctx* c, mcl_csc* A, float r, void* stream) {
+    if (!c) return MCL_ERR_INVALID;
+    mcl_status st;
+    if ((st = check_csc(c, A, "A"))) return st;
+    if (!(r > 0.0f && r <= 1.0e6f)) return fail(c, MCL_ERR_INVALID, "inflation must be > 0");
+    CUDA_TRY(c, cudaSetDevice(c->device));
+    launch_inflate_normalize(A->n, A->colptr, A->val, r, (cudaStream_t)stream);
+    return check_launch(c, "inflate_normalize");
+}
+
+mcl_status mcl_chaos(mcl_ctx* c, const mcl_csc* A, double* chaos, double* chaos_cols,
+                     void* stream) {
+    if (!c) return MCL_ERR_INVALID;
+    mcl_status st;
+    if ((st = check_csc(c, A, "A"))) return st;
+    if (!chaos) return fail(c, MCL_ERR_INVALID, "chaos is NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    CUDA_TRY(c, cudaSetDevice(c->device));
+    if (!ensure(c, c->ctr, sizeof(DevCounters), s)) return fail(c, MCL_ERR_OOM, "scratch");
+    DevCounters* ctr = (DevCounters*)c->ctr.p;
+    CUDA_TRY(c, cudaMemsetAsync(ctr, 0, sizeof(DevCounters), s));
+    launch_chaos(A->n, A->colptr, A->val, chaos_cols, ctr, s);
+    if ((st = check_launch(c, "chaos"))) return st;
+    if ((st = read_counters(c, s))) return st;
+    *chaos = chaos_from_bits(c->hctr->chaos_bits);
+    return MCL_OK;
+}
+
+mcl_status mcl_components(mcl_ctx* c, const mcl_csc* A, int32_t* labels, void* stream) {
+    if (!c) return MCL_ERR_INVALID;
+    mcl_status st;
+    if ((st = check_csc(c, A, "A"))) return st;
+    if (A->n > 0 && !labels) return fail(c, MCL_ERR_INVALID, "labels is NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    CUDA_TRY(c, cudaSetDevice(c->device));
+    if (!ensure(c, c->ctr, sizeof(DevCounters), s)) return fail(c, MCL_ERR_OOM, "scratch");
+    DevCounters* ctr = (DevCounters*)c->ctr.p;
+    CUDA_TRY(c, cudaMemsetAsync(ctr, 0, sizeof(DevCounters), s));
+    launch_components(view(A), labels, ctr, s);
+    if ((st = check_launch(c, "components"))) return st;
+    if ((st = read_counters(c, s))) return st;
+    return err_flags(c, c->hctr->err);
+}
+
+static void free_csc(mcl_ctx* c, mcl_csc* M, cudaStream_t s) {
+    dev_free(c, M->colptr, s);
+    dev_free(c, M->rowidx, s);
+    dev_free(c, M->val, s);
+    M->colptr = nullptr;
+    M->rowidx = nullptr;
+    M->val = nullptr;
+}
+
+mcl_status mcl_run(mcl_ctx* c, const mcl_csc* A0, const int32_t* comp_offsets, int32_t ncomp,
+                   const mcl_params* prm, int32_t* labels, int32_t* iters, double* chaos_hist,
+                   mcl_csc* final_out, void* stream) {
+    if (!c) return MCL_ERR_INVALID;
+    mcl_status st;
+    if ((st = check_csc(c, A0, "A0"))) return st;
+    if (!prm || prm->max_iters < 1) return fail(c, MCL_ERR_INVALID, "max_iters must be >= 1");
+    if (A0->n > 0 && !labels) return fail(c, MCL_ERR_INVALID, "labels is NULL");
+    if (comp_offsets && ncomp < 1) return fail(c, MCL_ERR_INVALID, "ncomp must be >= 1");
+    cudaStream_t s = (cudaStream_t)stream;
+    mcl_csc cur = *A0;
+    bool owned = false;
+    int it = 0;
+    double ch = 0.0;
+    bool converged = false;
+    while (it < prm->max_iters) {
+        mcl_csc nxt{};
+        st = expand_impl(c, &cur, prm, &nxt, &ch, s, nullptr);
+        if (st) {
+            if (owned) free_csc(c, &cur, s);
+            return st;
+        }
+        if (owned) free_csc(c, &cur, s);
+        cur = nxt;
+        owned = true;
+        if (chaos_hist) chaos_hist[it] = ch;
+        ++it;
+        if (ch < prm->chaos_eps) {
+            converged = true;
+            break;
+        }
+    }
+    c->stats.iterations = it;
+    if (iters) *iters = it;
+    st = mcl_components(c, &cur, labels, stream);
+    if (st) {
+        if (owned) free_csc(c, &cur, s);
+        return st;
+    }
+    if (final_out)
+        *final_out = cur;
+    else if (owned)
+        free_csc(c, &cur, s);
+    if (!converged)
+        return fail(c, MCL_ERR_NOT_CONVERGED, "max_iters reached with chaos %.3e", ch);
+    return MCL_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,309 @@
+// Device building blocks shared by the MCL kernels (sm_103a).
+//
+// Ranking keys: an entry (row i, value v >= 0) of a column is packed as
+//     key = (bits(v) << 32) | (0x7FFFFFFF - i)
+// so that key order (descending) is value descending, then row ascending --
+// the order in which the prune rule ranks a column (Alg. 1, Prune; equal
+// values keep the smaller row).  For v >= 0 the IEEE bit pattern is
+// monotone in v.  Keys of distinct rows are distinct, and every key is >= 1.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace mcl {
+
+constexpr unsigned FULL = 0xffffffffu;
+constexpr uint64_t EMPTY_SLOT = 0x00000000FFFFFFFFull;  // key -1, value +0.0f
+
+__device__ __forceinline__ uint64_t make_key(float v, int row) {
+    return ((uint64_t)__float_as_uint(v) << 32) | (uint32_t)(0x7FFFFFFF - row);
+}
+__device__ __forceinline__ int key_row(uint64_t k) { return 0x7FFFFFFF - (int)(uint32_t)k; }
+__device__ __forceinline__ float key_val(uint64_t k) { return __uint_as_float((uint32_t)(k >> 32)); }
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+    unsigned m;
+    asm volatile("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+template <typename V>
+__device__ __forceinline__ V warp_sum(V x) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(FULL, x, o);
+    return x;
+}
+template <typename V>
+__device__ __forceinline__ V warp_max(V x) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        V y = __shfl_xor_sync(FULL, x, o);
+        x = y > x ? y : x;
+    }
+    return x;
+}
+template <typename V>
+__device__ __forceinline__ V warp_min(V x) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        V y = __shfl_xor_sync(FULL, x, o);
+        x = y < x ? y : x;
+    }
+    return x;
+}
+
+// Scratch the block-level helpers use (lives in shared memory).
+struct BlockScratch {
+    double d[4][33];
+    long long q[4][33];
+    uint64_t sel_prefix;
+    int sel_need;
+    int sel_done;
+    double sel_target;
+    int sel_found;
+    int sel_above;
+    int cnt;
+    int pad;
+};
+
+// Sums of up to four doubles and four integers over the block (two barriers).
+template <int T>
+__device__ __forceinline__ void block_sum(double* dv, int nd, long long* qv, int nq,
+                                          BlockScratch* bs) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    constexpr int NW = T / 32;
+    for (int a = 0; a < nd; ++a) {
+        double x = warp_sum(dv[a]);
+        if (lane == 0) bs->d[a][warp] = x;
+    }
+    for (int a = 0; a < nq; ++a) {
+        long long x = warp_sum(qv[a]);
+        if (lane == 0) bs->q[a][warp] = x;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        for (int a = 0; a < nd; ++a) {
+            double x = lane < NW ? bs->d[a][lane] : 0.0;
+            x = warp_sum(x);
+            if (lane == 0) bs->d[a][32] = x;
+        }
+        for (int a = 0; a < nq; ++a) {
+            long long x = lane < NW ? bs->q[a][lane] : 0ll;
+            x = warp_sum(x);
+            if (lane == 0) bs->q[a][32] = x;
+        }
+    }
+    __syncthreads();
+    for (int a = 0; a < nd; ++a) dv[a] = bs->d[a][32];
+    for (int a = 0; a < nq; ++a) qv[a] = bs->q[a][32];
+}
+
+template <int T>
+__device__ __forceinline__ double block_max_d(double x, BlockScratch* bs) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    constexpr int NW = T / 32;
+    x = warp_max(x);
+    if (lane == 0) bs->d[3][warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        double y = lane < NW ? bs->d[3][lane] : -1.0e300;
+        y = warp_max(y);
+        if (lane == 0) bs->d[3][32] = y;
+    }
+    __syncthreads();
+    return bs->d[3][32];
+}
+
+// Element i of the concatenation A[0..na) ++ B[0..nb).
+__device__ __forceinline__ uint64_t cat_at(const uint64_t* A, int na, const uint64_t* B, int i) {
+    return i < na ? A[i] : B[i - na];
+}
+
+// Radix select by count over the distinct keys of A ++ B: returns kappa with
+// #{x : x >= kappa} == M exactly (1 <= M <= na + nb).  Most-significant
+// byte first; stops as soon as the chosen bucket holds exactly the keys
+// still needed, returning its prefix with zero low bits.
+template <int T>
+__device__ uint64_t block_select_count(const uint64_t* A, int na, const uint64_t* B, int nb, int M,
+                                       unsigned* hist, BlockScratch* bs) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tot = na + nb;
+    uint64_t prefix = 0;
+    int need = M;
+    for (int shift = 56; shift >= 0; shift -= 8) {
+        const uint64_t hmask = (shift == 56) ? 0ull : (~0ull << (shift + 8));
+        for (int i = tid; i < 256; i += T) hist[i] = 0u;
+        __syncthreads();
+        for (int i = tid; i < tot; i += T) {
+            uint64_t x = cat_at(A, na, B, i);
+            if ((x & hmask) == prefix) atomicAdd(&hist[(x >> shift) & 255u], 1u);
+        }
+        __syncthreads();
+        if (warp == 0) {
+            // lane l owns buckets 255-8l ... 248-8l, scanned from the top
+            int c[8];
+            int lsum = 0;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                c[q] = (int)hist[255 - 8 * lane - q];
+                lsum += c[q];
+            }
+            int incl = lsum;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                int y = __shfl_up_sync(FULL, incl, o);
+                if (lane >= o) incl += y;
+            }
+            int before = incl - lsum;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                if (before < need && before + c[q] >= need) {
+                    int d = 255 - 8 * lane - q;
+                    bs->sel_prefix = prefix | ((uint64_t)d << shift);
+                    bs->sel_need = need - before;
+                    bs->sel_done = (c[q] == need - before);
+                }
+                before += c[q];
+            }
+        }
+        __syncthreads();
+        prefix = bs->sel_prefix;
+        need = bs->sel_need;
+        if (bs->sel_done) break;
+    }
+    __syncthreads();
+    return prefix;
+}
+
+// Radix select by mass over the distinct keys of A[0..na): the smallest m
+// such that the m largest keys carry value mass >= target (target > 0).
+// Returns 1 and sets *kappa (a lower bound whose >= set is exactly those m
+// keys) and *m; returns 0 if the total mass is below target.
+template <int T>
+__device__ int block_select_mass(const uint64_t* A, int na, double target, uint64_t* kappa,
+                                 int* m, unsigned* hist, double* mhist, BlockScratch* bs) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    uint64_t prefix = 0;
+    double need = target;
+    int above = 0;
+    int found = 1;
+    for (int shift = 56; shift >= 0; shift -= 8) {
+        const uint64_t hmask = (shift == 56) ? 0ull : (~0ull << (shift + 8));
+        for (int i = tid; i < 256; i += T) {
+            hist[i] = 0u;
+            mhist[i] = 0.0;
+        }
+        __syncthreads();
+        for (int i = tid; i < na; i += T) {
+            uint64_t x = A[i];
+            if ((x & hmask) == prefix) {
+                unsigned b = (unsigned)((x >> shift) & 255u);
+                atomicAdd(&hist[b], 1u);
+                atomicAdd(&mhist[b], (double)key_val(x));
+            }
+        }
+        __syncthreads();
+        if (warp == 0) {
+            int c[8];
+            double mm[8];
+            double lsum = 0.0;
+            int lcnt = 0;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                c[q] = (int)hist[255 - 8 * lane - q];
+                mm[q] = mhist[255 - 8 * lane - q];
+                lsum += mm[q];
+                lcnt += c[q];
+            }
+            double incl = lsum;
+            int inclc = lcnt;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                double y = __shfl_up_sync(FULL, incl, o);
+                int yc = __shfl_up_sync(FULL, inclc, o);
+                if (lane >= o) {
+                    incl += y;
+                    inclc += yc;
+                }
+            }
+            double before = __shfl_up_sync(FULL, incl, 1);
+            int beforec = __shfl_up_sync(FULL, inclc, 1);
+            if (lane == 0) {
+                before = 0.0;
+                beforec = 0;
+            }
+            int hitq = -1;
+            double hb = 0.0;
+            int hbc = 0;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                if (hitq < 0) {
+                    if (c[q] > 0 && before + mm[q] >= need) {
+                        hitq = q;
+                        hb = before;
+                        hbc = beforec;
+                    } else {
+                        before += mm[q];
+                        beforec += c[q];
+                    }
+                }
+            }
+            unsigned hm = __ballot_sync(FULL, hitq >= 0);
+            if (hm == 0u) {
+                if (lane == 0) bs->sel_found = 0;
+            } else if (lane == __ffs(hm) - 1) {
+                int d = 255 - 8 * lane - hitq;
+                bs->sel_prefix = prefix | ((uint64_t)d << shift);
+                bs->sel_target = need - hb;
+                bs->sel_above = above + hbc;
+                bs->sel_need = c[hitq];
+                bs->sel_found = 1;
+            }
+        }
+        __syncthreads();
+        if (!bs->sel_found) {
+            found = 0;
+            break;
+        }
+        prefix = bs->sel_prefix;
+        need = bs->sel_target;
+        above = bs->sel_above;
+        if (bs->sel_need == 1) break;  // one key left in the bucket: the crossing key
+    }
+    __syncthreads();
+    if (found) {
+        *kappa = prefix;
+        *m = above + 1;
+    }
+    return found;
+}
+
+// Ascending bitonic sort of s[0..P) (P a power of two) by the block.
+template <int T>
+__device__ void block_bitonic_sort(uint64_t* s, int P) {
+    for (int k = 2; k <= P; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = threadIdx.x; i < P; i += T) {
+                int ixj = i ^ j;
+                if (ixj > i) {
+                    uint64_t a = s[i], b = s[ixj];
+                    bool up = (i & k) == 0;
+                    if ((a > b) == up) {
+                        s[i] = b;
+                        s[ixj] = a;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
+
+__host__ __device__ __forceinline__ int next_pow2(int x) {
+    int p = 1;
+    while (p < x) p <<= 1;
+    return p;
+}
+
+}  // namespace mcl

@@ -1,0 +1,130 @@
+// Internal interface between the C ABI (mcl_api.cu) and the kernels
+// (mcl_kernels.cu, mcl_cc.cu).  Not installed; not part of the ABI.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace mcl {
+
+// Accumulator configurations of the fused numeric pass: hash / dense table
+// of H slots (8 bytes each) per CTA of T threads.
+constexpr int NCONF = 4;
+constexpr int NZ = 8;                    // size classes per configuration
+constexpr int NBUCKET = NCONF * NZ;
+__host__ __device__ constexpr int conf_h(int c) {
+    return c == 0 ? 512 : c == 1 ? 2048 : c == 2 ? 8192 : 16384;
+}
+__host__ __device__ constexpr int conf_t(int c) {
+    return c == 0 ? 128 : c == 1 ? 256 : c == 2 ? 512 : 1024;
+}
+
+// device-side counters (one small block of memory per context)
+struct DevCounters {
+    unsigned long long misses;       // columns whose nnz exceeded the estimate
+    unsigned long long splits;       // range overflows resolved by halving
+    unsigned long long flops;        // sum of flops_j
+    unsigned long long nnz_b;        // sum of nnz(B_*j)
+    unsigned long long chaos_bits;   // max chaos_j as ordered bits (>= 0)
+    unsigned long long cap_total;    // sum of output capacities
+    unsigned long long nnz_out;      // sum of kept counts
+    int max_deg;
+    int max_span;
+    unsigned err;                    // bit flags (ERR_*)
+    int pad;
+    int bin_cnt[NBUCKET];
+    int bin_off[NBUCKET + 1];
+    int bin_fill[NBUCKET];
+    int conf_ctr[NCONF];
+    int work_ctr;
+};
+
+enum : unsigned {
+    ERR_COLPTR = 1u,      // colptr not monotone / out of [0, nnz]
+    ERR_ROW_RANGE = 2u,   // row index outside [0, n)
+    ERR_ROW_ORDER = 4u,   // rows not strictly increasing in a column
+    ERR_VALUE = 8u,       // value negative, NaN or infinite
+    ERR_INTERNAL = 16u,   // device consistency check failed
+    ERR_TIMEOUT = 32u,    // bounded loop gave up
+    ERR_CURSOR = 64u,     // cursor scratch too small
+};
+
+struct CscView {
+    int32_t n;
+    int64_t nnz;
+    const int64_t* colptr;
+    const int32_t* rowidx;
+    const float* val;
+};
+
+struct PruneParams {
+    float theta;
+    int32_t K;
+    float p;
+    int32_t Krec;
+    int32_t ksel;   // max(K, Krec)
+    float r;
+    int32_t inflate;
+};
+
+struct ExpandBuffers {
+    int64_t* flops;     // [n]
+    int32_t* rlo;       // [n]
+    int32_t* rhi;       // [n]
+    int64_t* cap;       // [n]   output capacity min(Krec, flops, span)
+    int64_t* off;       // [n+1] exclusive scan of cap
+    int64_t* est;       // [n]   size estimate used for binning
+    int32_t* bucket;    // [n]
+    int32_t* work;      // [n]
+    int32_t* kept;      // [n]
+    double* chaos;      // [n]
+    int64_t* bnnz;      // [n]
+    int32_t* tmp_row;   // [cap_total]
+    float* tmp_val;     // [cap_total]
+    int32_t* cursors;   // [grid * 2 * cur_stride]
+    int64_t cur_stride;
+    int64_t* scan_tmp;  // tile sums
+    int64_t scan_tmp_len;
+    DevCounters* ctr;
+    const uint8_t* active;  // optional per-column mask (NULL: all active)
+};
+
+// --- launch accounting (every launcher adds the kernels it starts) ---
+void count_launches(int k);
+long long launches_total();
+
+// --- launchers (mcl_kernels.cu) ---
+void launch_colstats(const CscView& A, const PruneParams& pp, const ExpandBuffers& b,
+                     int num_sms, cudaStream_t s);
+int64_t scan_tmp_len_for(int64_t n);
+template <typename TIn>
+void launch_exclusive_scan(const TIn* in, int64_t n, int64_t* out, int64_t* tmp,
+                           unsigned long long* total, cudaStream_t s);
+void launch_symbolic(const CscView& A, const ExpandBuffers& b, int64_t* nnz_out, int num_sms,
+                     int grid_cap, cudaStream_t s);
+int symbolic_grid(int num_sms);
+void launch_scale_est(int32_t n, int64_t* est, int milli, cudaStream_t s);
+void launch_est_from_flops(const CscView& A, const ExpandBuffers& b, cudaStream_t s);
+void launch_binning(const CscView& A, const PruneParams& pp, const ExpandBuffers& b, int mask,
+                    cudaStream_t s);
+int numeric_grid(int conf, int ksel, int num_sms);
+size_t numeric_smem(int conf, int ksel);
+bool conf_allowed(int conf, int ksel);
+void launch_numeric(int conf, const CscView& A, const PruneParams& pp, const ExpandBuffers& b,
+                    int grid, cudaStream_t s);
+void launch_compact(const CscView& A, const ExpandBuffers& b, const int64_t* colptr_out,
+                    int32_t* row_out, float* val_out, cudaStream_t s);
+void launch_finalize_stats(int32_t n, const ExpandBuffers& b, cudaStream_t s);
+void launch_prune_cap(const CscView& B, int32_t Krec, const ExpandBuffers& b, cudaStream_t s);
+void launch_prune(const CscView& B, const PruneParams& pp, const ExpandBuffers& b, int num_sms,
+                  cudaStream_t s);
+void launch_inflate_normalize(int32_t n, const int64_t* colptr, float* val, float r,
+                              cudaStream_t s);
+void launch_chaos(int32_t n, const int64_t* colptr, const float* val, double* chaos_cols,
+                  DevCounters* ctr, cudaStream_t s);
+void launch_fill_colptr(int32_t n, int64_t* colptr, cudaStream_t s);
+
+// --- components (mcl_cc.cu) ---
+void launch_components(const CscView& A, int32_t* labels, DevCounters* ctr, cudaStream_t s);
+
+}  // namespace mcl

@@ -1,0 +1,299 @@
+"""GPU parity tests of the fused MCL iteration and the standalone entry
+points, through the C ABI, against the FP64 oracle fed the same input.
+
+Tolerance: 1e-5 relative per value (FP32 values and accumulation against
+FP64); kept patterns identical except ambiguous boundary entries (see
+tests/parity.py).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2002_10083_gb300 import synth
+from tests.parity import compare_iteration
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+RTOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2002_10083_gb300 import mcl
+    c = mcl.Context(0)
+    yield c
+    c.close()
+
+
+def _prm(theta=1e-4, K=100, p=0.9, Krec=0, r=2.0, eps=1e-3, iters=30):
+    from paper_2002_10083_gb300 import mcl
+    return mcl.Params(threshold=theta, select_k=K, recover_pct=p, recover_k=Krec, inflation=r,
+                      chaos_eps=eps, max_iters=iters)
+
+
+def _oprm(p):
+    return oracle.Params(theta=float(np.float32(p.threshold)), K=p.select_k,
+                         p=float(np.float32(p.recover_pct)),
+                         K_rec=p.recover_k if p.recover_k > 0 else None,
+                         r=float(np.float32(p.inflation)), eps=p.chaos_eps, max_iters=p.max_iters)
+
+
+def _dev(A):
+    from paper_2002_10083_gb300 import mcl
+    return mcl.DeviceCSC.from_host(A)
+
+
+def _check(ctx, A, prm, cols=None):
+    A32 = A.with_val32()
+    D = _dev(A32)
+    out, ch = ctx.expand(D, prm)
+    torch.cuda.synchronize()
+    G = out.to_host()
+    rep, res = compare_iteration(A32, G, _oprm(prm), cols=cols, rtol=RTOL)
+    assert rep.ok(), rep.failures[:5]
+    if cols is None and A.n:
+        och = float(res.chaos.max())
+        # chaos_j <= max a; value errors of rtol bound its error by 3 rtol max a
+        assert abs(ch - och) <= 3 * RTOL * max(1.0, och) + 1e-12, (ch, och)
+    return rep, G, ch
+
+
+@pytest.mark.parametrize("n,dens,seed", [(300, 0.03, 0), (1000, 0.01, 1), (3000, 0.004, 2),
+                                         (777, 0.02, 3)])
+@pytest.mark.parametrize("K,p,theta", [(100, 0.9, 1e-4), (20, 0.5, 1e-3), (1, 0.9, 1e-4),
+                                       (4096, 1.0, 0.0), (64, 0.0, 0.0)])
+def test_expand_random(ctx, n, dens, seed, K, p, theta):
+    A = synth.random_sparse(n, dens, seed=seed, w="lognormal")
+    rep, G, _ = _check(ctx, A, _prm(theta=theta, K=K, p=p))
+    assert rep.entries > 0
+
+
+@pytest.mark.parametrize("mask", [0b0100, 0b1000, 0b1100, 0b1111])
+@pytest.mark.parametrize("scale", [1000, 20])
+def test_expand_multi_range_and_splits(ctx, mask, scale):
+    """Columns far larger than the accumulator: several row ranges, and with
+    a deliberate 50x under-estimate, overflow + range splitting."""
+    from paper_2002_10083_gb300 import mcl
+    A = synth.chung_lu(n=20000, mean=60.0, d_max=2000, seed=5)
+    try:
+        ctx.set_option(mcl.OPT_CONF_MASK, mask)
+        ctx.set_option(mcl.OPT_EST_SCALE, scale)
+        cols = np.random.default_rng(0).choice(A.n, 600, replace=False).astype(np.int32)
+        rep, G, _ = _check(ctx, A, _prm(K=300, p=0.9), cols=cols)
+        st = ctx.stats()
+        if scale < 1000:
+            assert st["range_splits"] > 0 and st["estimator_misses"] > 0
+    finally:
+        ctx.set_option(mcl.OPT_CONF_MASK, 0xF)
+        ctx.set_option(mcl.OPT_EST_SCALE, 1000)
+
+
+@pytest.mark.parametrize("sizing", [0, 1])
+def test_sizing_modes_same_result(ctx, sizing):
+    from paper_2002_10083_gb300 import mcl
+    A = synth.random_sparse(2000, 0.01, seed=9, w="lognormal").with_val32()
+    D = _dev(A)
+    try:
+        ctx.set_option(mcl.OPT_SIZING, sizing)
+        out, ch = ctx.expand(D, _prm(K=50))
+    finally:
+        ctx.set_option(mcl.OPT_SIZING, -1)
+    ref, ch2 = ctx.expand(D, _prm(K=50))
+    assert torch.equal(out.colptr, ref.colptr) and torch.equal(out.rowidx, ref.rowidx)
+    assert torch.allclose(out.val, ref.val, rtol=RTOL, atol=0)
+
+
+def test_planted2k_iterations_and_clusters(ctx):
+    """The 2,000-vertex planted partition: every GPU iteration matches the
+    oracle fed the GPU's own input; the clusters equal the oracle's run."""
+    A = synth.config("planted2k").with_val32()
+    prm = _prm(theta=1e-4, K=100, p=0.9, iters=30)
+    D = _dev(A)
+    it = 0
+    host_in = A
+    while it < prm.max_iters:
+        out, ch = ctx.expand(D, prm)
+        G = out.to_host()
+        rep, res = compare_iteration(host_in, G, _oprm(prm), rtol=RTOL)
+        assert rep.ok(), (it, rep.failures[:5])
+        it += 1
+        D, host_in = out, G
+        if ch < prm.chaos_eps:
+            break
+    lab_gpu, iters, hist, final, notconv = ctx.run(_dev(A), prm)
+    assert not notconv and iters == it
+    _, o_iters, o_hist, o_lab = oracle.run_mcl(A, _oprm(prm))
+    assert iters == o_iters
+    assert np.array_equal(lab_gpu.cpu().numpy(), o_lab)
+
+
+@pytest.mark.parametrize("sizes", [[4, 8, 16], [32, 64, 4, 8], [64] * 20])
+def test_cliques_fixed_point(ctx, sizes):
+    A = synth.cliques(sizes)
+    prm = _prm(theta=1e-4, K=max(sizes), p=0.9)
+    lab, iters, hist, final, notconv = ctx.run(_dev(A), prm)
+    assert iters == 1 and hist[0] == 0.0
+    starts = np.concatenate([[0], np.cumsum(sizes)[:-1]])
+    assert np.array_equal(lab.cpu().numpy(), np.repeat(starts, sizes))
+    F = final.to_host()
+    np.testing.assert_array_equal(F.val, A.val.astype(np.float32).astype(np.float64))
+
+
+@pytest.mark.parametrize("seed", range(4))
+@pytest.mark.parametrize("K,p,theta,Krec", [(5, 0.9, 0.3, 0), (1, 0.5, 0.0, 0), (8, 0.0, 0.2, 0),
+                                            (3, 0.95, 0.9, 6), (4096, 1.0, 0.0, 0)])
+def test_prune_standalone(ctx, seed, K, p, theta, Krec):
+    B = synth.random_csc(400, 400, 0.05, seed=seed, lo=0.0, hi=1.0, empty_cols=(3, 17))
+    # a column of exact ties
+    B.val[B.colptr[5]:B.colptr[6]] = 0.25
+    B32 = B.with_val32()
+    prm = _prm(theta=theta, K=K, p=p, Krec=Krec)
+    out = ctx.prune_select_recover(_dev(B32), prm)
+    G = out.to_host()
+    ms, orow, oval, _ = oracle.prune_cols(B32, _oprm(prm))
+    for j in range(B.n):
+        s, e = G.colptr[j], G.colptr[j + 1]
+        assert e - s == ms[j], j
+        assert np.array_equal(G.rowidx[s:e], orow[j, :ms[j]]), j
+        np.testing.assert_array_equal(G.val[s:e], oval[j, :ms[j]])
+
+
+def test_inflate_normalize_and_chaos_standalone(ctx):
+    A = synth.random_csc(500, 500, 0.03, seed=4, lo=0.01, hi=2.0, empty_cols=(7,)).with_val32()
+    D = _dev(A)
+    ctx.inflate_normalize(D, 2.0)
+    G = D.to_host()
+    ref, och = oracle.inflate_normalize(A, 2.0)
+    np.testing.assert_allclose(G.val, ref.val, rtol=RTOL, atol=0)
+    ch, cols = ctx.chaos(D, per_column=True)
+    gch = oracle.chaos_cols(G)
+    np.testing.assert_allclose(cols.cpu().numpy(), gch, rtol=1e-12, atol=1e-15)
+    assert abs(ch - gch.max()) <= 1e-15
+
+
+def test_chaos_golden_columns(ctx, golden_dir):
+    import os
+    rows, vals, cp, want = [], [], [0], []
+    for line in open(os.path.join(golden_dir, "chaos_cases.txt")):
+        line = line.strip()
+        if not line or line.startswith("#"):
+            continue
+        v, w = line.split("|")
+        v = [float(x) for x in v.split()]
+        rows += list(range(len(v)))
+        vals += v
+        cp.append(cp[-1] + len(v))
+        want.append(float(w))
+    n = max(len(cp) - 1, max(rows) + 1)
+    cp += [cp[-1]] * (n + 1 - len(cp))
+    A = synth.CSC(n=n, colptr=np.array(cp, np.int64), rowidx=np.array(rows, np.int32),
+                  val=np.array(vals))
+    ch, cols = ctx.chaos(_dev(A), per_column=True)
+    c = cols.cpu().numpy()
+    for i, w in enumerate(want):
+        # FP32 inputs: a value like 0.9 is not exact in FP32
+        assert abs(c[i] - w) < 1e-6, (i, c[i], w)
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_components(ctx, seed):
+    A = synth.random_csc(5000, 5000, 0.0003, seed=seed)
+    lab = ctx.components(_dev(A)).cpu().numpy()
+    assert np.array_equal(lab, oracle.components(A))
+
+
+def test_symbolic(ctx):
+    A = synth.random_sparse(3000, 0.01, seed=3)
+    fl, nz = ctx.symbolic(_dev(A))
+    of, on = oracle.symbolic_cols(A)
+    assert np.array_equal(fl.cpu().numpy(), of)
+    assert np.array_equal(nz.cpu().numpy(), on)
+
+
+def test_symbolic_windows_large_span(ctx):
+    # spans above one bitmap window (524,288 rows) use several windows
+    A = synth.chung_lu(n=700000, mean=8.0, d_max=500, seed=1)
+    fl, nz = ctx.symbolic(_dev(A))
+    cols = np.random.default_rng(1).choice(A.n, 3000, replace=False).astype(np.int32)
+    of, on = oracle.symbolic_cols(A, cols=cols)
+    assert np.array_equal(fl.cpu().numpy()[cols], of)
+    assert np.array_equal(nz.cpu().numpy()[cols], on)
+
+
+def test_edge_cases(ctx):
+    from paper_2002_10083_gb300 import mcl
+    prm = _prm(K=10)
+    # n = 0
+    E = synth.CSC(n=0, colptr=np.zeros(1, np.int64), rowidx=np.zeros(0, np.int32), val=np.zeros(0))
+    out, ch = ctx.expand(_dev(E), prm)
+    assert out.n == 0 and out.nnz == 0 and ch == 0.0
+    # empty columns and a single entry
+    A = synth.random_csc(50, 50, 0.1, seed=2, lo=0.1, hi=1.0, empty_cols=(0, 1, 49))
+    _check(ctx, A, prm)
+    # all-equal values: ties at the k-th value resolved by the smaller row
+    A = synth.random_sparse(200, 0.1, seed=3, w="one", loop="one")
+    _check(ctx, A, _prm(K=7, p=0.5))
+
+
+@pytest.mark.parametrize("kind", ["order", "range", "value", "nan", "colptr"])
+def test_invalid_input_rejected(ctx, kind):
+    from paper_2002_10083_gb300 import mcl
+    A = synth.random_sparse(100, 0.05, seed=1)
+    rowidx = A.rowidx.copy()
+    val = A.val.copy()
+    colptr = A.colptr.copy()
+    s = colptr[10]
+    if kind == "order":
+        rowidx[s], rowidx[s + 1] = rowidx[s + 1], rowidx[s]
+    elif kind == "range":
+        rowidx[colptr[20 + 1] - 1] = 100
+    elif kind == "value":
+        val[5] = -0.5
+    elif kind == "nan":
+        val[7] = np.nan
+    elif kind == "colptr":
+        colptr[30] = colptr[31] + 1
+    B = synth.CSC(n=A.n, colptr=colptr, rowidx=rowidx, val=val)
+    with pytest.raises(mcl.MclError) as ei:
+        ctx.expand(_dev(B), _prm(K=10))
+    assert ei.value.status == 1
+    # the context stays usable
+    _check(ctx, A, _prm(K=10))
+
+
+def test_bad_params_rejected(ctx):
+    from paper_2002_10083_gb300 import mcl
+    A = _dev(synth.random_sparse(50, 0.1, seed=1))
+    for bad in (dict(K=0), dict(K=5000), dict(p=1.5), dict(theta=-1.0), dict(r=0.0)):
+        with pytest.raises(mcl.MclError):
+            ctx.expand(A, _prm(**bad))
+
+
+@pytest.fixture(scope="module")
+def zipf1m():
+    return synth.config("zipf1m").with_val32()
+
+
+def test_zipf1m_one_iteration_sampled(ctx, zipf1m):
+    """The 1M-vertex power-law workload at full size: sampled columns
+    against the oracle, every output column sums to 1."""
+    A = zipf1m
+    prm = _prm(theta=1e-4, K=1100, p=0.9)
+    D = _dev(A)
+    out, ch = ctx.expand(D, prm)
+    torch.cuda.synchronize()
+    G = out.to_host()
+    sums = np.add.reduceat(G.val, G.colptr[:-1]) if G.nnz else np.zeros(0)
+    nzc = np.diff(G.colptr) > 0
+    np.testing.assert_allclose(sums[nzc], 1.0, rtol=0, atol=2e-5)
+    rng = np.random.default_rng(2002)
+    deg = np.diff(A.colptr)
+    cols = np.concatenate([rng.choice(A.n, 1500, replace=False),
+                           np.argsort(-deg)[:40]]).astype(np.int32)  # include the hubs
+    rep, res = compare_iteration(A, G, _oprm(prm), cols=cols, rtol=RTOL)
+    assert rep.ok(), rep.failures[:5]
+    st = ctx.stats()
+    assert st["flops"] == int((deg.astype(np.int64) ** 2).sum())
