@@ -104,14 +104,14 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def make_workload(name: str, seed: int = 0):
+def make_workload(name: str, seed: int = 0, n: int | None = None):
     from paper_2002_10083_gb300 import synth
     cache = os.environ.get("MCL_BENCH_CACHE", "/tmp/mcl_bench_cache")
-    path = os.path.join(cache, f"{name}_s{seed}.npz")
+    path = os.path.join(cache, f"{name}_n{n}_s{seed}.npz")
     if os.path.exists(path):
         z = np.load(path)
         return synth.CSC(n=int(z["n"]), colptr=z["colptr"], rowidx=z["rowidx"], val=z["val"])
-    A = synth.config(name, seed=seed)
+    A = synth.config(name, seed=seed, **({"n": n} if n else {}))
     A = synth.CSC(n=A.n, colptr=A.colptr, rowidx=A.rowidx, val=A.val.astype(np.float32))
     try:
         os.makedirs(cache, exist_ok=True)
@@ -148,7 +148,7 @@ def run_reference(args):
     rank, _, world = _env_rank()
     if rank != 0:
         return 0
-    A = make_workload(args.workload)
+    A = make_workload(args.workload, n=args.n)
     per_step = float(os.environ.get("MCL_REF_STEP_SECONDS", "6"))
     vals = []
     for i in range(args.warmup + args.steps):
@@ -183,7 +183,7 @@ def run_gpu(args):
     from paper_2002_10083_gb300 import mcl
     dev = local
     torch.cuda.set_device(dev)
-    A = make_workload(args.workload)
+    A = make_workload(args.workload, n=args.n)
     n, nnz = A.n, A.nnz
     D = mcl.DeviceCSC.from_host(A, device=f"cuda:{dev}")
     ctx = mcl.Context(dev)
@@ -238,7 +238,7 @@ def run_gpu(args):
     hcp = torch.from_numpy(A.colptr).pin_memory()
     hri = torch.from_numpy(A.rowidx).pin_memory()
     hva = torch.from_numpy(A.val.astype(np.float32)).pin_memory()
-    e2e_steps = max(1, min(args.steps, 3))
+    e2e_steps = 0 if args.no_e2e else max(1, min(args.steps, 3))
     out_bytes = 0
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -256,13 +256,13 @@ def run_gpu(args):
         torch.cuda.synchronize()
         out_bytes = ocp.numel() * 8 + ori.numel() * 4 + ova.numel() * 4
         del out, Dh
-    e2e_ms = (time.perf_counter() - t0) * 1000.0 / e2e_steps
+    e2e_ms = (time.perf_counter() - t0) * 1000.0 / max(e2e_steps, 1)
     in_bytes = hcp.numel() * 8 + hri.numel() * 4 + hva.numel() * 4
 
     if rank != 0:
         return 0
     gflops = 2.0 * flops / (ms / 1000.0) / 1e9 * world
-    e2e_gflops = 2.0 * flops / (e2e_ms / 1000.0) / 1e9 * world
+    e2e_gflops = 2.0 * flops / (e2e_ms / 1000.0) / 1e9 * world if e2e_steps else None
     peak, peak_kind = _peaks()
     t_num = statistics.median(ms_num)
     b_alg = 8 * nnz + 8 * flops + 8 * nnz_out + 16 * n
@@ -289,8 +289,9 @@ def run_gpu(args):
                      "algorithmic_bytes": b_alg, "kernel_ms": round(t_num, 3),
                      "peak_kind": peak_kind},
         "cpu_baseline": cpu,
-        "e2e": {"value": round(e2e_gflops, 2), "unit": "GFLOP/s", "h2d_bytes_per_step": in_bytes,
-                "d2h_bytes_per_step": out_bytes, "ms_per_step": round(e2e_ms, 3)},
+        "e2e": ({"value": round(e2e_gflops, 2), "unit": "GFLOP/s", "h2d_bytes_per_step": in_bytes,
+                 "d2h_bytes_per_step": out_bytes, "ms_per_step": round(e2e_ms, 3)}
+                if e2e_steps else None),
         "gpu_launches": int(launches),
         "clocks": clocks,
         "stage_ms": {k: round(v, 3) for k, v in ctx.stats().items() if k.startswith("ms_")},
@@ -312,6 +313,8 @@ def main():
     ap.add_argument("--sizing", default=None, choices=[None, "exact", "flops"])
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--n", type=int, default=None, help="override the vertex count (profiling cases)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

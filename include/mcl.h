@@ -208,13 +208,70 @@ mcl_status mcl_symbolic(mcl_ctx* ctx, const mcl_csc* A, int64_t* flops, int64_t*
  *   4 MCL_OPT_EST_SCALE  multiply every size estimate by value/1000 (1000 =
  *                        unchanged); a deliberate mis-estimate exercises the
  *                        accumulator overflow path (results stay exact)
+ *   5 MCL_OPT_ITERATION  iteration index fed to the estimator's features by
+ *                        mcl_expand (default 1; mcl_run sets it itself)
  * Returns MCL_ERR_INVALID for an unknown option or value.
  */
 #define MCL_OPT_SIZING 1
 #define MCL_OPT_CONF_MASK 2
 #define MCL_OPT_VALIDATE 3
 #define MCL_OPT_EST_SCALE 4
+#define MCL_OPT_ITERATION 5
 mcl_status mcl_set_option(mcl_ctx* ctx, int option, int64_t value);
+
+/*
+ * Learned output-size estimator (sizing without the symbolic pass).
+ *
+ * Each column j of A is described by 16 features computed in O(nnz(A_*j))
+ * (column and referenced-column sizes, value mass, spans, iteration,
+ * previous compression factor); a 16 -> 64 -> 64 -> 2 MLP with ReLU, BF16
+ * weights and FP32 accumulation predicts y0 = log(1 + nnz((AA)_*j)) and
+ * y1 = log cf_j (cf = flops / nnz, Section II notation).  It replaces the
+ * exact symbolic SpGEMM (Sections II and V: the per-iteration memory
+ * estimate) when sizing the accumulators; the exact pass remains available
+ * (prm->use_estimator = 0, or mcl_symbolic) and judges the estimate.
+ * Estimates never change results: an under-estimate narrows the numeric
+ * pass's row ranges, an over-estimate widens its tables.
+ *
+ * Weights: MCL_MLP_NPARAM values laid out W1 [64 x 16] (row = output
+ * unit), b1 [64], W2 [64 x 64], b2 [64], W3 [2 x 64], b3 [2], as BF16 bit
+ * patterns (uint16).  norm: mu[16] then sigma[16] (FP32); the network sees
+ * (x - mu) / sigma.  All pointers below are DEVICE pointers unless marked
+ * host.  None of these calls synchronises.
+ */
+#define MCL_MLP_NPARAM 5378
+#define MCL_NFEATURES 16
+
+/* Install estimator weights (host arrays; copied) and the safety factor s
+ * (estimate = ceil(expm1(y0) * s), clamped to [1, min(flops_j, span_j)]). */
+mcl_status mcl_estimator_load(mcl_ctx* ctx, const uint16_t* w_bf16_host, const float* norm_host,
+                              float safety);
+
+/* Features of every column of A into feats (float[n * 16], row-major per
+ * column).  iteration >= 1; prev_logcf: float[n] or NULL (feature 13 = 0). */
+mcl_status mcl_features(mcl_ctx* ctx, const mcl_csc* A, int32_t iteration,
+                        const float* prev_logcf, float* feats, void* stream);
+
+/* MLP forward: out (float[n * 2]) = (y0, y1) for each row of feats. */
+mcl_status mcl_mlp_forward(mcl_ctx* ctx, const float* feats, int64_t n, const uint16_t* w_bf16,
+                           const float* norm, float* out, void* stream);
+
+/* MLP backward for training: adds d/dw of scale * sum_samples sum_outputs
+ * (y - target)^2 into grad (float[MCL_MLP_NPARAM]) and the unscaled sum
+ * into *loss (double).  targets: float[n * 2]. */
+mcl_status mcl_mlp_backward(mcl_ctx* ctx, const float* feats, const float* targets, int64_t n,
+                            const uint16_t* w_bf16, const float* norm, float scale, float* grad,
+                            double* loss, void* stream);
+
+/* One Adam step (step >= 1) on FP32 master weights; writes their BF16
+ * rounding (nearest even) into w_bf16.  m, v: float[MCL_MLP_NPARAM]. */
+mcl_status mcl_adam_step(mcl_ctx* ctx, float* master, float* m, float* v, const float* grad,
+                         int64_t step, float lr, float beta1, float beta2, float eps,
+                         uint16_t* w_bf16, void* stream);
+
+/* The size estimate the numeric pass would use with the loaded estimator
+ * (iteration from MCL_OPT_ITERATION), into est (int64[n]). */
+mcl_status mcl_estimate(mcl_ctx* ctx, const mcl_csc* A, int64_t* est, void* stream);
 
 /* Statistics of the last mcl_expand / mcl_run on ctx. */
 mcl_status mcl_get_stats(mcl_ctx* ctx, mcl_stats* stats);

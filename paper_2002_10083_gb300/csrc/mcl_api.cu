@@ -40,10 +40,11 @@ struct mcl_ctx {
     int validate = 1;
     int est_milli = 1000;   // estimate scale (test knob)
     // learned estimator (weights on device)
-    Buf mlp_w;
+    Buf mlp_w, mlp_norm, colmax, feats, prev_logcf;
     int has_estimator = 0;
     float est_safety = 1.25f;
-    Buf feats, pred;
+    int iteration = 1;
+    int prev_valid = 0;
 };
 
 namespace {
@@ -209,10 +210,20 @@ int max_numeric_grid(mcl_ctx* c, int ksel) {
 
 }  // namespace
 
-// Learned-estimator hook (mcl_estimator.cu): fills b.est from features and
-// the MLP; returns MCL_OK or an error.
-mcl_status mcl_internal_estimate(mcl_ctx* c, const mcl_csc* A, const ExpandBuffers& b,
-                                 cudaStream_t s);
+// Learned estimate: features -> MLP -> b.est (needs colstats done).
+static mcl_status internal_estimate(mcl_ctx* c, const mcl_csc* A, const ExpandBuffers& b,
+                                    cudaStream_t s) {
+    const size_t n1 = (size_t)A->n + 1;
+    if (!ensure(c, c->colmax, n1 * 4, s) || !ensure(c, c->feats, n1 * 4 * MCL_NFEATURES, s))
+        return fail(c, MCL_ERR_OOM, "estimator scratch allocation failed");
+    const float* prev = (c->prev_valid && c->prev_logcf.bytes >= n1 * 4)
+                            ? (const float*)c->prev_logcf.p : nullptr;
+    launch_colmax_features(view(A), c->iteration, prev, (float*)c->colmax.p, (float*)c->feats.p, s);
+    launch_mlp_forward((const float*)c->feats.p, A->n, (const uint16_t*)c->mlp_w.p,
+                       (const float*)c->mlp_norm.p, nullptr, b.est, c->est_safety, b.flops, b.rlo,
+                       b.rhi, s);
+    return check_launch(c, "estimator");
+}
 
 extern "C" {
 
@@ -254,7 +265,7 @@ void mcl_destroy(mcl_ctx* c) {
     Buf* all[] = {&c->flops, &c->rlo,     &c->rhi,     &c->cap,     &c->off,  &c->est,
                   &c->bucket, &c->work,   &c->kept,    &c->chaos,   &c->bnnz, &c->tmp_row,
                   &c->tmp_val, &c->cursors, &c->scan,  &c->ctr,     &c->active, &c->mlp_w,
-                  &c->feats,  &c->pred};
+                  &c->mlp_norm, &c->colmax, &c->feats, &c->prev_logcf};
     for (Buf* b : all) dev_free(c, b->p, 0);
     cudaDeviceSynchronize();
     for (auto& e : c->ev) cudaEventDestroy(e);
@@ -287,6 +298,10 @@ mcl_status mcl_set_option(mcl_ctx* c, int option, int64_t value) {
         case 4:  // estimate scale in thousandths (1000 = as estimated)
             if (value < 1 || value > 1000000) return fail(c, MCL_ERR_INVALID, "bad scale");
             c->est_milli = (int)value;
+            return MCL_OK;
+        case 5:  // iteration index for the estimator's features
+            if (value < 1 || value > 1000000) return fail(c, MCL_ERR_INVALID, "bad iteration");
+            c->iteration = (int)value;
             return MCL_OK;
         default:
             return fail(c, MCL_ERR_INVALID, "unknown option %d", option);
@@ -334,7 +349,7 @@ static mcl_status expand_impl(mcl_ctx* c, const mcl_csc* A, const mcl_params* pr
     if (sizing == 2) {
         if (!c->has_estimator)
             return fail(c, MCL_ERR_INVALID, "use_estimator set but no estimator loaded");
-        if ((st = mcl_internal_estimate(c, A, b, s))) return st;
+        if ((st = internal_estimate(c, A, b, s))) return st;
     } else if (sizing == 1) {
         launch_est_from_flops(Av, b, s);
     } else {
@@ -546,6 +561,90 @@ mcl_status mcl_components(mcl_ctx* c, const mcl_csc* A, int32_t* labels, void* s
     return err_flags(c, c->hctr->err);
 }
 
+mcl_status mcl_estimator_load(mcl_ctx* c, const uint16_t* w, const float* norm, float safety) {
+    if (!c) return MCL_ERR_INVALID;
+    if (!w || !norm) return fail(c, MCL_ERR_INVALID, "weights / norm is NULL");
+    if (!(safety >= 0.01f && safety <= 1000.0f)) return fail(c, MCL_ERR_INVALID, "bad safety");
+    for (int i = 0; i < MCL_NFEATURES; ++i)
+        if (!(norm[MCL_NFEATURES + i] > 0.0f)) return fail(c, MCL_ERR_INVALID, "sigma must be > 0");
+    CUDA_TRY(c, cudaSetDevice(c->device));
+    if (!ensure(c, c->mlp_w, MCL_MLP_NPARAM * 2, 0) ||
+        !ensure(c, c->mlp_norm, 2 * MCL_NFEATURES * 4, 0))
+        return fail(c, MCL_ERR_OOM, "estimator allocation failed");
+    CUDA_TRY(c, cudaMemcpy(c->mlp_w.p, w, MCL_MLP_NPARAM * 2, cudaMemcpyHostToDevice));
+    CUDA_TRY(c, cudaMemcpy(c->mlp_norm.p, norm, 2 * MCL_NFEATURES * 4, cudaMemcpyHostToDevice));
+    c->est_safety = safety;
+    c->has_estimator = 1;
+    return MCL_OK;
+}
+
+mcl_status mcl_features(mcl_ctx* c, const mcl_csc* A, int32_t iteration, const float* prev_logcf,
+                        float* feats, void* stream) {
+    if (!c) return MCL_ERR_INVALID;
+    mcl_status st;
+    if ((st = check_csc(c, A, "A"))) return st;
+    if (A->n > 0 && !feats) return fail(c, MCL_ERR_INVALID, "feats is NULL");
+    if (iteration < 1) return fail(c, MCL_ERR_INVALID, "iteration must be >= 1");
+    cudaStream_t s = (cudaStream_t)stream;
+    CUDA_TRY(c, cudaSetDevice(c->device));
+    if (!ensure(c, c->colmax, ((size_t)A->n + 1) * 4, s)) return fail(c, MCL_ERR_OOM, "scratch");
+    launch_colmax_features(view(A), iteration, prev_logcf, (float*)c->colmax.p, feats, s);
+    return check_launch(c, "features");
+}
+
+mcl_status mcl_mlp_forward(mcl_ctx* c, const float* feats, int64_t n, const uint16_t* w,
+                           const float* norm, float* out, void* stream) {
+    if (!c) return MCL_ERR_INVALID;
+    if (n < 0 || (n > 0 && (!feats || !w || !norm || !out)))
+        return fail(c, MCL_ERR_INVALID, "bad forward arguments");
+    CUDA_TRY(c, cudaSetDevice(c->device));
+    launch_mlp_forward(feats, n, w, norm, out, nullptr, 1.0f, nullptr, nullptr, nullptr,
+                       (cudaStream_t)stream);
+    return check_launch(c, "mlp_forward");
+}
+
+mcl_status mcl_mlp_backward(mcl_ctx* c, const float* feats, const float* targets, int64_t n,
+                            const uint16_t* w, const float* norm, float scale, float* grad,
+                            double* loss, void* stream) {
+    if (!c) return MCL_ERR_INVALID;
+    if (n < 0 || (n > 0 && (!feats || !targets || !w || !norm || !grad || !loss)))
+        return fail(c, MCL_ERR_INVALID, "bad backward arguments");
+    CUDA_TRY(c, cudaSetDevice(c->device));
+    launch_mlp_backward(feats, targets, n, w, norm, scale, grad, loss, (cudaStream_t)stream);
+    return check_launch(c, "mlp_backward");
+}
+
+mcl_status mcl_adam_step(mcl_ctx* c, float* master, float* m, float* v, const float* grad,
+                         int64_t step, float lr, float beta1, float beta2, float eps,
+                         uint16_t* w, void* stream) {
+    if (!c) return MCL_ERR_INVALID;
+    if (!master || !m || !v || !grad || !w || step < 1)
+        return fail(c, MCL_ERR_INVALID, "bad adam arguments");
+    CUDA_TRY(c, cudaSetDevice(c->device));
+    launch_adam(master, m, v, grad, step, lr, beta1, beta2, eps, w, (cudaStream_t)stream);
+    return check_launch(c, "adam");
+}
+
+mcl_status mcl_estimate(mcl_ctx* c, const mcl_csc* A, int64_t* est, void* stream) {
+    if (!c) return MCL_ERR_INVALID;
+    mcl_status st;
+    if ((st = check_csc(c, A, "A"))) return st;
+    if (!c->has_estimator) return fail(c, MCL_ERR_INVALID, "no estimator loaded");
+    if (A->n > 0 && !est) return fail(c, MCL_ERR_INVALID, "est is NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    CUDA_TRY(c, cudaSetDevice(c->device));
+    if ((st = ensure_columns(c, A->n, s))) return st;
+    ExpandBuffers b = buffers(c);
+    PruneParams pp{};
+    pp.Krec = 1;
+    CUDA_TRY(c, cudaMemsetAsync(c->ctr.p, 0, sizeof(DevCounters), s));
+    launch_colstats(view(A), pp, b, c->num_sms, s);
+    if ((st = read_counters(c, s))) return st;
+    if ((st = err_flags(c, c->hctr->err))) return st;
+    b.est = est;
+    return internal_estimate(c, A, b, s);
+}
+
 static void free_csc(mcl_ctx* c, mcl_csc* M, cudaStream_t s) {
     dev_free(c, M->colptr, s);
     dev_free(c, M->rowidx, s);
@@ -570,11 +669,24 @@ mcl_status mcl_run(mcl_ctx* c, const mcl_csc* A0, const int32_t* comp_offsets, i
     int it = 0;
     double ch = 0.0;
     bool converged = false;
+    const int saved_iter = c->iteration;
+    c->prev_valid = 0;
     while (it < prm->max_iters) {
         mcl_csc nxt{};
+        c->iteration = it + 1;
         st = expand_impl(c, &cur, prm, &nxt, &ch, s, nullptr);
+        if (!st && prm->use_estimator) {
+            // the compression factor of this iteration feeds the next one's features
+            if (ensure(c, c->prev_logcf, ((size_t)cur.n + 1) * 4, s)) {
+                launch_logcf(cur.n, (const int64_t*)c->flops.p, (const int64_t*)c->bnnz.p,
+                             (float*)c->prev_logcf.p, s);
+                c->prev_valid = 1;
+            }
+        }
         if (st) {
             if (owned) free_csc(c, &cur, s);
+            c->iteration = saved_iter;
+            c->prev_valid = 0;
             return st;
         }
         if (owned) free_csc(c, &cur, s);
@@ -587,6 +699,8 @@ mcl_status mcl_run(mcl_ctx* c, const mcl_csc* A0, const int32_t* comp_offsets, i
             break;
         }
     }
+    c->iteration = saved_iter;
+    c->prev_valid = 0;
     c->stats.iterations = it;
     if (iters) *iters = it;
     st = mcl_components(c, &cur, labels, stream);

@@ -124,6 +124,20 @@ void launch_chaos(int32_t n, const int64_t* colptr, const float* val, double* ch
                   DevCounters* ctr, cudaStream_t s);
 void launch_fill_colptr(int32_t n, int64_t* colptr, cudaStream_t s);
 
+// --- estimator (mcl_estimator.cu) ---
+void launch_colmax_features(const CscView& A, int32_t iteration, const float* prev_logcf,
+                            float* colmax, float* feats, cudaStream_t s);
+void launch_mlp_forward(const float* feats, int64_t n, const uint16_t* wbits, const float* norm,
+                        float* out, int64_t* est, float safety, const int64_t* flops,
+                        const int32_t* rlo, const int32_t* rhi, cudaStream_t s);
+void launch_mlp_backward(const float* feats, const float* targets, int64_t n,
+                         const uint16_t* wbits, const float* norm, float scale, float* grad,
+                         double* loss, cudaStream_t s);
+void launch_adam(float* master, float* m, float* v, const float* grad, int64_t step, float lr,
+                 float b1, float b2, float eps, uint16_t* wbits, cudaStream_t s);
+void launch_logcf(int32_t n, const int64_t* flops, const int64_t* bnnz, float* logcf,
+                  cudaStream_t s);
+
 // --- components (mcl_cc.cu) ---
 void launch_components(const CscView& A, int32_t* labels, DevCounters* ctr, cudaStream_t s);
 

@@ -21,7 +21,7 @@ from . import build as _build
 MCL_OK = 0
 STATUS = {0: "MCL_OK", 1: "MCL_ERR_INVALID", 2: "MCL_ERR_OOM", 3: "MCL_ERR_CUDA",
           4: "MCL_ERR_TIMEOUT", 5: "MCL_ERR_NOT_CONVERGED", 6: "MCL_ERR_INTERNAL"}
-OPT_SIZING, OPT_CONF_MASK, OPT_VALIDATE, OPT_EST_SCALE = 1, 2, 3, 4
+OPT_SIZING, OPT_CONF_MASK, OPT_VALIDATE, OPT_EST_SCALE, OPT_ITERATION = 1, 2, 3, 4, 5
 SIZING_PARAMS, SIZING_EXACT, SIZING_FLOPS = -1, 0, 1
 MAX_SELECT_K = 4096
 
@@ -79,7 +79,16 @@ SIGNATURES = {
     "mcl_symbolic": (ctypes.c_int, [P, ctypes.POINTER(_Csc), P, P, P]),
     "mcl_get_stats": (ctypes.c_int, [P, ctypes.POINTER(_Stats)]),
     "mcl_set_option": (ctypes.c_int, [P, ctypes.c_int, ctypes.c_int64]),
+    "mcl_estimator_load": (ctypes.c_int, [P, P, P, ctypes.c_float]),
+    "mcl_features": (ctypes.c_int, [P, ctypes.POINTER(_Csc), ctypes.c_int32, P, P, P]),
+    "mcl_mlp_forward": (ctypes.c_int, [P, P, ctypes.c_int64, P, P, P, P]),
+    "mcl_mlp_backward": (ctypes.c_int, [P, P, P, ctypes.c_int64, P, P, ctypes.c_float, P, P, P]),
+    "mcl_adam_step": (ctypes.c_int, [P, P, P, P, P, ctypes.c_int64, ctypes.c_float, ctypes.c_float,
+                                     ctypes.c_float, ctypes.c_float, P, P]),
+    "mcl_estimate": (ctypes.c_int, [P, ctypes.POINTER(_Csc), P, P]),
 }
+MLP_NPARAM = 5378
+NFEATURES = 16
 
 _lib = None
 _lib_lock = threading.Lock()
@@ -301,6 +310,51 @@ class Context:
             self._check(st)
         final = self._adopt_csc(out) if keep_final and out.colptr else None
         return lab[:A0.n], it.value, list(hist[:it.value]), final, st == 5
+
+    # learned estimator ------------------------------------------------------
+    def estimator_load(self, w_bf16: np.ndarray, norm: np.ndarray, safety: float):
+        w = np.ascontiguousarray(w_bf16, dtype=np.uint16)
+        nm = np.ascontiguousarray(norm, dtype=np.float32)
+        assert w.size == MLP_NPARAM and nm.size == 2 * NFEATURES
+        self._check(self.lib.mcl_estimator_load(self.h, w.ctypes.data_as(P), nm.ctypes.data_as(P),
+                                                float(safety)))
+
+    def features(self, A: DeviceCSC, iteration: int = 1, prev_logcf=None, stream=None):
+        a = A.c()
+        f = torch.empty((max(A.n, 1), NFEATURES), dtype=torch.float32, device=A.colptr.device)
+        self._check(self.lib.mcl_features(self.h, ctypes.byref(a), int(iteration),
+                                          P(prev_logcf.data_ptr()) if prev_logcf is not None else None,
+                                          P(f.data_ptr()), _stream_ptr(stream)))
+        return f[:A.n]
+
+    def mlp_forward(self, feats, w_bf16_dev, norm_dev, stream=None):
+        n = feats.shape[0]
+        out = torch.empty((max(n, 1), 2), dtype=torch.float32, device=feats.device)
+        self._check(self.lib.mcl_mlp_forward(self.h, P(feats.data_ptr()), n, P(w_bf16_dev.data_ptr()),
+                                             P(norm_dev.data_ptr()), P(out.data_ptr()),
+                                             _stream_ptr(stream)))
+        return out[:n]
+
+    def mlp_backward(self, feats, targets, w_bf16_dev, norm_dev, scale, grad, loss, stream=None):
+        n = feats.shape[0]
+        self._check(self.lib.mcl_mlp_backward(self.h, P(feats.data_ptr()), P(targets.data_ptr()), n,
+                                              P(w_bf16_dev.data_ptr()), P(norm_dev.data_ptr()),
+                                              float(scale), P(grad.data_ptr()), P(loss.data_ptr()),
+                                              _stream_ptr(stream)))
+
+    def adam_step(self, master, m, v, grad, step, lr, w_bf16_dev, beta1=0.9, beta2=0.999,
+                  eps=1e-8, stream=None):
+        self._check(self.lib.mcl_adam_step(self.h, P(master.data_ptr()), P(m.data_ptr()),
+                                           P(v.data_ptr()), P(grad.data_ptr()), int(step), float(lr),
+                                           float(beta1), float(beta2), float(eps),
+                                           P(w_bf16_dev.data_ptr()), _stream_ptr(stream)))
+
+    def estimate(self, A: DeviceCSC, stream=None):
+        a = A.c()
+        est = torch.empty(max(A.n, 1), dtype=torch.int64, device=A.colptr.device)
+        self._check(self.lib.mcl_estimate(self.h, ctypes.byref(a), P(est.data_ptr()),
+                                          _stream_ptr(stream)))
+        return est[:A.n]
 
     def stats(self) -> dict:
         s = _Stats()
