@@ -101,7 +101,7 @@ typedef struct {
     int64_t nnz_b;            /* nnz(A A) before pruning (exact, counted in the numeric pass) */
     int64_t nnz_out;          /* nnz after prune */
     int64_t estimator_misses; /* columns whose nnz exceeded the size estimate */
-    int64_t range_splits;     /* accumulator overflows resolved by narrowing the row range */
+    int64_t range_splits;     /* row windows cut because their entries exceeded the capacity */
     double chaos;             /* max_j chaos_j */
     float ms_colstats, ms_estimate, ms_bin, ms_numeric, ms_compact, ms_chaos, ms_total;
     int32_t bins_used;
@@ -202,8 +202,8 @@ mcl_status mcl_symbolic(mcl_ctx* ctx, const mcl_csc* A, int64_t* flops, int64_t*
  * Tuning options of a context (not part of the method):
  *   1 MCL_OPT_SIZING     -1 follow prm->use_estimator (default), 0 exact
  *                        symbolic pass, 1 the flops bound min(flops_j, span_j)
- *   2 MCL_OPT_CONF_MASK  bit mask of accumulator configurations (bit 2 or 3
- *                        must stay set)
+ *   2 MCL_OPT_CONF_MASK  bit mask of numeric-pass configurations (bit 0:
+ *                        small CTA and window, bit 1: large; not 0)
  *   3 MCL_OPT_VALIDATE   1 (default) validate inputs
  *   4 MCL_OPT_EST_SCALE  multiply every size estimate by value/1000 (1000 =
  *                        unchanged); a deliberate mis-estimate exercises the

@@ -30,13 +30,14 @@ struct mcl_ctx {
     char err[512] = {0};
     // scratch
     Buf flops, rlo, rhi, cap, off, est, bucket, work, kept, chaos, bnnz, tmp_row, tmp_val,
-        cursors, scan, ctr, active;
+        cursors, scan, ctr, active, bucket_row, bucket_val, woff;
+    size_t bucket_budget = (size_t)32 << 30;  // bytes of product buckets (large config)
     DevCounters* hctr = nullptr;  // pinned host mirror
     mcl_stats stats{};
     cudaEvent_t ev[8] = {};
     // options
     int sizing = -1;        // -1: from params (exact or learned); 0 exact; 1 flops bound
-    int conf_mask = 0xF;    // accumulator configurations allowed
+    int conf_mask = 0x3;    // numeric configurations allowed
     int validate = 1;
     int est_milli = 1000;   // estimate scale (test knob)
     // learned estimator (weights on device)
@@ -168,6 +169,10 @@ ExpandBuffers buffers(mcl_ctx* c) {
     b.scan_tmp = (int64_t*)c->scan.p;
     b.ctr = (DevCounters*)c->ctr.p;
     b.active = nullptr;
+    b.bucket_row = nullptr;
+    b.bucket_val = nullptr;
+    b.woff = nullptr;
+    b.bucket_cap = 0;
     return b;
 }
 
@@ -200,7 +205,6 @@ double chaos_from_bits(unsigned long long b) {
 int max_numeric_grid(mcl_ctx* c, int ksel) {
     int g = 0;
     for (int q = 0; q < NCONF; ++q) {
-        if (!conf_allowed(q, ksel)) continue;
         int gq = numeric_grid(q, ksel, c->num_sms);
         if (gq > g) g = gq;
     }
@@ -262,7 +266,8 @@ void mcl_destroy(mcl_ctx* c) {
     if (!c) return;
     cudaSetDevice(c->device);
     cudaDeviceSynchronize();
-    Buf* all[] = {&c->flops, &c->rlo,     &c->rhi,     &c->cap,     &c->off,  &c->est,
+    Buf* all[] = {&c->bucket_row, &c->bucket_val, &c->woff,
+                  &c->flops, &c->rlo,     &c->rhi,     &c->cap,     &c->off,  &c->est,
                   &c->bucket, &c->work,   &c->kept,    &c->chaos,   &c->bnnz, &c->tmp_row,
                   &c->tmp_val, &c->cursors, &c->scan,  &c->ctr,     &c->active, &c->mlp_w,
                   &c->mlp_norm, &c->colmax, &c->feats, &c->prev_logcf};
@@ -288,9 +293,9 @@ mcl_status mcl_set_option(mcl_ctx* c, int option, int64_t value) {
             if (value < -1 || value > 1) return fail(c, MCL_ERR_INVALID, "bad sizing option");
             c->sizing = (int)value;
             return MCL_OK;
-        case 2:  // accumulator configuration mask
-            if ((value & 0xC) == 0) return fail(c, MCL_ERR_INVALID, "conf mask must keep conf 2 or 3");
-            c->conf_mask = (int)(value & 0xF);
+        case 2:  // numeric configuration mask
+            if ((value & 0x3) == 0) return fail(c, MCL_ERR_INVALID, "conf mask selects nothing");
+            c->conf_mask = (int)(value & 0x3);
             return MCL_OK;
         case 3:
             c->validate = value != 0;
@@ -338,7 +343,7 @@ static mcl_status expand_impl(mcl_ctx* c, const mcl_csc* A, const mcl_params* pr
     const int grid_max = max_numeric_grid(c, pp.ksel);
     if (!ensure(c, c->tmp_row, (size_t)cap_total * 4 + 4, s) ||
         !ensure(c, c->tmp_val, (size_t)cap_total * 4 + 4, s) ||
-        !ensure(c, c->cursors, (size_t)grid_max * 2 * b.cur_stride * 4, s))
+        !ensure(c, c->cursors, (size_t)grid_max * 6 * b.cur_stride * 4, s))
         return fail(c, MCL_ERR_OOM, "scratch allocation failed (capacity %lld)",
                     (long long)cap_total);
     b.tmp_row = (int32_t*)c->tmp_row.p;
@@ -363,9 +368,29 @@ static mcl_status expand_impl(mcl_ctx* c, const mcl_csc* A, const mcl_params* pr
     cudaEventRecord(c->ev[3], s);
     int used = 0;
     for (int q = NCONF - 1; q >= 0; --q) {
-        if (!conf_allowed(q, pp.ksel) || !((c->conf_mask >> q) & 1)) continue;
+        if (!((c->conf_mask >> q) & 1)) continue;
         int g = numeric_grid(q, pp.ksel, c->num_sms);
-        launch_numeric(q, Av, pp, b, g, s);
+        ExpandBuffers bq = b;
+        bq.bucket_row = nullptr;
+        bq.bucket_val = nullptr;
+        bq.woff = nullptr;
+        bq.bucket_cap = 0;
+        if (q == NCONF - 1) {
+            // product buckets for multi-window columns of the large configuration
+            const int64_t maxf = (int64_t)c->hctr->max_flops;
+            int64_t capb = (int64_t)(c->bucket_budget / ((size_t)g * 8));
+            if (capb > maxf) capb = maxf;
+            if (capb >= 1024 &&
+                ensure(c, c->bucket_row, (size_t)g * capb * 4, s) &&
+                ensure(c, c->bucket_val, (size_t)g * capb * 4, s) &&
+                ensure(c, c->woff, (size_t)g * (WINDOW_MAX + 1) * 4, s)) {
+                bq.bucket_row = (int32_t*)c->bucket_row.p;
+                bq.bucket_val = (float*)c->bucket_val.p;
+                bq.woff = (int32_t*)c->woff.p;
+                bq.bucket_cap = capb;
+            }
+        }
+        launch_numeric(q, Av, pp, bq, g, s);
         ++used;
     }
     if ((st = check_launch(c, "numeric"))) return st;
@@ -452,7 +477,7 @@ mcl_status mcl_symbolic(mcl_ctx* c, const mcl_csc* A, int64_t* flops, int64_t* n
     if ((st = err_flags(c, c->hctr->err))) return st;
     b.cur_stride = ((c->hctr->max_deg + 31) & ~31) + 32;
     const int grid = symbolic_grid(c->num_sms);
-    if (!ensure(c, c->cursors, (size_t)grid * 2 * b.cur_stride * 4, s))
+    if (!ensure(c, c->cursors, (size_t)grid * 6 * b.cur_stride * 4, s))
         return fail(c, MCL_ERR_OOM, "cursor scratch allocation failed");
     b.cursors = (int32_t*)c->cursors.p;
     if (nnz_out) launch_symbolic(Av, b, nnz_out, c->num_sms, grid, s);

@@ -123,7 +123,8 @@ __device__ __forceinline__ uint64_t cat_at(const uint64_t* A, int na, const uint
 // Radix select by count over the distinct keys of A ++ B: returns kappa with
 // #{x : x >= kappa} == M exactly (1 <= M <= na + nb).  Most-significant
 // byte first; stops as soon as the chosen bucket holds exactly the keys
-// still needed, returning its prefix with zero low bits.
+// still needed, returning its prefix with zero low bits.  Histogram updates
+// are aggregated per warp over lanes with the same digit.
 template <int T>
 __device__ uint64_t block_select_count(const uint64_t* A, int na, const uint64_t* B, int nb, int M,
                                        unsigned* hist, BlockScratch* bs) {
@@ -135,9 +136,17 @@ __device__ uint64_t block_select_count(const uint64_t* A, int na, const uint64_t
         const uint64_t hmask = (shift == 56) ? 0ull : (~0ull << (shift + 8));
         for (int i = tid; i < 256; i += T) hist[i] = 0u;
         __syncthreads();
-        for (int i = tid; i < tot; i += T) {
-            uint64_t x = cat_at(A, na, B, i);
-            if ((x & hmask) == prefix) atomicAdd(&hist[(x >> shift) & 255u], 1u);
+        for (int base = 0; base < tot; base += T) {
+            const int i = base + tid;
+            const bool valid = i < tot;
+            const uint64_t x = valid ? cat_at(A, na, B, i) : 0ull;
+            const bool in = valid && (x & hmask) == prefix;
+            const unsigned act = __ballot_sync(FULL, in);
+            if (in) {
+                const unsigned dg = (unsigned)((x >> shift) & 255u);
+                const unsigned grp = __match_any_sync(act, dg);
+                if (__ffs(grp) - 1 == lane) atomicAdd(&hist[dg], (unsigned)__popc(grp));
+            }
         }
         __syncthreads();
         if (warp == 0) {
@@ -179,35 +188,72 @@ __device__ uint64_t block_select_count(const uint64_t* A, int na, const uint64_t
 // Radix select by mass over the distinct keys of A[0..na): the smallest m
 // such that the m largest keys carry value mass >= target (target > 0).
 // Returns 1 and sets *kappa (a lower bound whose >= set is exactly those m
-// keys) and *m; returns 0 if the total mass is below target.
+// keys) and *m; returns 0 if the total mass is below target.  Masses are
+// summed in 64-bit fixed point scaled by a power of two that keeps every
+// value below 2^50 (exact integer sums, no floating-point atomics); the
+// truncation error of a cumulative mass is below na * 2^-50 * max value.
 template <int T>
 __device__ int block_select_mass(const uint64_t* A, int na, double target, uint64_t* kappa,
-                                 int* m, unsigned* hist, double* mhist, BlockScratch* bs) {
+                                 int* m, unsigned* hist, unsigned long long* mhist,
+                                 BlockScratch* bs) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    // largest key = largest value
+    uint64_t kmax = 0;
+    for (int i = tid; i < na; i += T) kmax = A[i] > kmax ? A[i] : kmax;
+    kmax = warp_max(kmax);
+    if (lane == 0) bs->q[3][warp] = (long long)kmax;
+    __syncthreads();
+    if (warp == 0) {
+        uint64_t y = lane < T / 32 ? (uint64_t)bs->q[3][lane] : 0ull;
+        y = warp_max(y);
+        if (lane == 0) bs->q[3][32] = (long long)y;
+    }
+    __syncthreads();
+    const float maxv = key_val((uint64_t)bs->q[3][32]);
+    int e = 0;
+    frexpf(maxv > 0.0f ? maxv : 1.0f, &e);  // maxv < 2^e
+    const double scale = ldexp(1.0, 50 - e);
+    const double tf = ceil(target * scale);
+    if (!(tf < 9.0e18)) {  // beyond any reachable sum
+        __syncthreads();
+        return 0;
+    }
+    unsigned long long need = (unsigned long long)tf;
     uint64_t prefix = 0;
-    double need = target;
     int above = 0;
     int found = 1;
     for (int shift = 56; shift >= 0; shift -= 8) {
         const uint64_t hmask = (shift == 56) ? 0ull : (~0ull << (shift + 8));
         for (int i = tid; i < 256; i += T) {
             hist[i] = 0u;
-            mhist[i] = 0.0;
+            mhist[i] = 0ull;
         }
         __syncthreads();
-        for (int i = tid; i < na; i += T) {
-            uint64_t x = A[i];
-            if ((x & hmask) == prefix) {
-                unsigned b = (unsigned)((x >> shift) & 255u);
-                atomicAdd(&hist[b], 1u);
-                atomicAdd(&mhist[b], (double)key_val(x));
+        for (int base = 0; base < na; base += T) {
+            const int i = base + tid;
+            const bool valid = i < na;
+            const uint64_t x = valid ? A[i] : 0ull;
+            const bool in = valid && (x & hmask) == prefix;
+            const unsigned act = __ballot_sync(FULL, in);
+            if (in) {
+                const unsigned dg = (unsigned)((x >> shift) & 255u);
+                const unsigned grp = __match_any_sync(act, dg);
+                // group sum of the fixed-point masses (< 2^50 each) as two
+                // 25-bit halves, each summed exactly in 32 bits
+                const unsigned long long fx = (unsigned long long)((double)key_val(x) * scale);
+                const unsigned lo25 = __reduce_add_sync(grp, (unsigned)(fx & 0x1FFFFFFull));
+                const unsigned hi25 = __reduce_add_sync(grp, (unsigned)(fx >> 25));
+                if (__ffs(grp) - 1 == lane) {
+                    atomicAdd(&hist[dg], (unsigned)__popc(grp));
+                    atomicAdd(&mhist[dg], ((unsigned long long)hi25 << 25) + lo25);
+                }
             }
         }
         __syncthreads();
         if (warp == 0) {
             int c[8];
-            double mm[8];
-            double lsum = 0.0;
+            unsigned long long mm[8];
+            unsigned long long lsum = 0;
             int lcnt = 0;
 #pragma unroll
             for (int q = 0; q < 8; ++q) {
@@ -216,25 +262,21 @@ __device__ int block_select_mass(const uint64_t* A, int na, double target, uint6
                 lsum += mm[q];
                 lcnt += c[q];
             }
-            double incl = lsum;
+            unsigned long long incl = lsum;
             int inclc = lcnt;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
-                double y = __shfl_up_sync(FULL, incl, o);
+                unsigned long long y = __shfl_up_sync(FULL, incl, o);
                 int yc = __shfl_up_sync(FULL, inclc, o);
                 if (lane >= o) {
                     incl += y;
                     inclc += yc;
                 }
             }
-            double before = __shfl_up_sync(FULL, incl, 1);
-            int beforec = __shfl_up_sync(FULL, inclc, 1);
-            if (lane == 0) {
-                before = 0.0;
-                beforec = 0;
-            }
+            unsigned long long before = incl - lsum;
+            int beforec = inclc - lcnt;
             int hitq = -1;
-            double hb = 0.0;
+            unsigned long long hb = 0;
             int hbc = 0;
 #pragma unroll
             for (int q = 0; q < 8; ++q) {
@@ -255,10 +297,11 @@ __device__ int block_select_mass(const uint64_t* A, int na, double target, uint6
             } else if (lane == __ffs(hm) - 1) {
                 int d = 255 - 8 * lane - hitq;
                 bs->sel_prefix = prefix | ((uint64_t)d << shift);
-                bs->sel_target = need - hb;
+                bs->sel_target = (double)(need - hb);
                 bs->sel_above = above + hbc;
                 bs->sel_need = c[hitq];
                 bs->sel_found = 1;
+                bs->q[2][32] = (long long)(need - hb);
             }
         }
         __syncthreads();
@@ -267,7 +310,7 @@ __device__ int block_select_mass(const uint64_t* A, int na, double target, uint6
             break;
         }
         prefix = bs->sel_prefix;
-        need = bs->sel_target;
+        need = (unsigned long long)bs->q[2][32];
         above = bs->sel_above;
         if (bs->sel_need == 1) break;  // one key left in the bucket: the crossing key
     }
@@ -298,6 +341,13 @@ __device__ void block_bitonic_sort(uint64_t* s, int P) {
             __syncthreads();
         }
     }
+}
+
+// Inflation (Alg. 1, Hadamard power r) of one FP32 value.
+__device__ __forceinline__ float inflate_value(float v, float r) {
+    if (r == 2.0f) return v * v;
+    if (r == 1.0f) return v;
+    return powf(v, r);
 }
 
 __host__ __device__ __forceinline__ int next_pow2(int x) {

@@ -7,18 +7,11 @@
 
 namespace mcl {
 
-// Accumulator configurations of the fused numeric pass: hash / dense table
-// of H slots (8 bytes each) per CTA of T threads.
-constexpr int NCONF = 4;
+// Configurations of the fused numeric pass (mcl_numeric.cu): 0 = small CTA
+// and window for small columns, 1 = large CTA and window for the rest.
+constexpr int NCONF = 2;
 constexpr int NZ = 8;                    // size classes per configuration
 constexpr int NBUCKET = NCONF * NZ;
-__host__ __device__ constexpr int conf_h(int c) {
-    return c == 0 ? 512 : c == 1 ? 2048 : c == 2 ? 8192 : 16384;
-}
-__host__ __device__ constexpr int conf_t(int c) {
-    return c == 0 ? 128 : c == 1 ? 256 : c == 2 ? 512 : 1024;
-}
-
 // device-side counters (one small block of memory per context)
 struct DevCounters {
     unsigned long long misses;       // columns whose nnz exceeded the estimate
@@ -28,6 +21,7 @@ struct DevCounters {
     unsigned long long chaos_bits;   // max chaos_j as ordered bits (>= 0)
     unsigned long long cap_total;    // sum of output capacities
     unsigned long long nnz_out;      // sum of kept counts
+    unsigned long long max_flops;    // max_j flops_j
     int max_deg;
     int max_span;
     unsigned err;                    // bit flags (ERR_*)
@@ -81,8 +75,12 @@ struct ExpandBuffers {
     int64_t* bnnz;      // [n]
     int32_t* tmp_row;   // [cap_total]
     float* tmp_val;     // [cap_total]
-    int32_t* cursors;   // [grid * 2 * cur_stride]
+    int32_t* cursors;   // per CTA: source metadata, 6 * cur_stride int32
     int64_t cur_stride;
+    int32_t* bucket_row;   // per CTA: bucket_cap products (row) of the current column
+    float* bucket_val;     // per CTA: bucket_cap products (a_ik * a_kj)
+    int32_t* woff;         // per CTA: window offsets into the bucket (WINDOW_MAX + 1)
+    int64_t bucket_cap;
     int64_t* scan_tmp;  // tile sums
     int64_t scan_tmp_len;
     DevCounters* ctr;
@@ -109,7 +107,9 @@ void launch_binning(const CscView& A, const PruneParams& pp, const ExpandBuffers
                     cudaStream_t s);
 int numeric_grid(int conf, int ksel, int num_sms);
 size_t numeric_smem(int conf, int ksel);
-bool conf_allowed(int conf, int ksel);
+int numeric_threads(int conf);
+constexpr int WINDOW_MAX = 4096;  // windows per column in bucket mode
+int conf_value_capacity(int conf);
 void launch_numeric(int conf, const CscView& A, const PruneParams& pp, const ExpandBuffers& b,
                     int grid, cudaStream_t s);
 void launch_compact(const CscView& A, const ExpandBuffers& b, const int64_t* colptr_out,

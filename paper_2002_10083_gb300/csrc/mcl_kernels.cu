@@ -44,7 +44,7 @@ __global__ void k_colstats(CscView A, int32_t Krec, ExpandBuffers b) {
     const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     DevCounters* C = b.ctr;
-    unsigned long long fl_acc = 0;
+    unsigned long long fl_acc = 0, fl_max = 0;
     int deg_max = 0, span_max = 0;
     if (gw == 0 && lane == 0) {
         if (A.colptr[0] != 0 || A.colptr[A.n] != A.nnz) set_err(C, ERR_COLPTR);
@@ -102,12 +102,14 @@ __global__ void k_colstats(CscView A, int32_t Krec, ExpandBuffers b) {
             if (b.active && !b.active[j]) cap = ce - cb;  // carried column: copied as is
             b.cap[j] = cap;
             fl_acc += (unsigned long long)f;
+            fl_max = fl_max > (unsigned long long)f ? fl_max : (unsigned long long)f;
             deg_max = max(deg_max, (int)(ce - cb));
             span_max = max(span_max, span);
         }
     }
     if (lane == 0) {
         if (fl_acc) atomicAdd(&C->flops, fl_acc);
+        if (fl_max) atomicMax(&C->max_flops, fl_max);
         atomicMax(&C->max_deg, deg_max);
         atomicMax(&C->max_span, span_max);
     }
@@ -402,29 +404,20 @@ void launch_est_from_flops(const CscView& A, const ExpandBuffers& b, cudaStream_
 // binning: configuration by estimated size, size classes for LPT order
 // ---------------------------------------------------------------------------
 
-__host__ __device__ inline bool conf_ok(int c, int ksel) { return conf_h(c) >= next_pow2(ksel); }
-
-bool conf_allowed(int conf, int ksel) { return conf_ok(conf, ksel); }
-
-__device__ __forceinline__ int bucket_of(int64_t est, int ksel, int mask) {
-    // smallest allowed configuration whose half-full table holds the
-    // estimate; otherwise the largest allowed one (several row ranges)
-    int c = -1, last = -1;
-    for (int q = 0; q < NCONF; ++q) {
-        if (!conf_ok(q, ksel) || !((mask >> q) & 1)) continue;
-        last = q;
-        if (c < 0 && est <= conf_h(q) / 2) c = q;
-    }
-    if (c < 0) c = last;
-    const int64_t per = conf_h(c) / 2;
-    int64_t R = (est + per - 1) / per;
-    if (R < 1) R = 1;
-    const int lg = 63 - __clzll((long long)R);
+// Configuration 0 (small CTA) takes columns whose estimate fits one small
+// window's value capacity and whose span needs few windows; configuration 1
+// takes the rest.  The size class orders work longest-first by flops_j.
+__device__ __forceinline__ int bucket_of(int64_t est, int64_t flops, int span, int mask) {
+    int c = 1;
+    if ((mask & 1) && est <= 512 && span <= 8 * 16384) c = 0;
+    if (!(mask & 2)) c = 0;
+    int64_t f = flops >> 12;
+    const int lg = f > 0 ? 63 - __clzll((long long)f) : 0;
     const int z = NZ - 1 - (lg < NZ - 1 ? lg : NZ - 1);
     return c * NZ + z;
 }
 
-__global__ void k_bin_count(int32_t n, int32_t ksel, int mask, ExpandBuffers b) {
+__global__ void k_bin_count(int32_t n, int mask, ExpandBuffers b) {
     __shared__ int hist[NBUCKET];
     for (int i = threadIdx.x; i < NBUCKET; i += blockDim.x) hist[i] = 0;
     __syncthreads();
@@ -434,7 +427,7 @@ __global__ void k_bin_count(int32_t n, int32_t ksel, int mask, ExpandBuffers b) 
             b.bucket[j] = -1;
             continue;
         }
-        int bk = bucket_of(b.est[j], ksel, mask);
+        int bk = bucket_of(b.est[j], b.flops[j], b.rhi[j] - b.rlo[j] + 1, mask);
         b.bucket[j] = bk;
         atomicAdd(&hist[bk], 1);
     }
@@ -479,7 +472,7 @@ void launch_binning(const CscView& A, const PruneParams& pp, const ExpandBuffers
     cudaMemsetAsync(b.ctr->bin_cnt, 0, sizeof(int) * NBUCKET, s);
     if (A.n > 0) {
         int64_t blocks = (A.n + 255) / 256;
-        k_bin_count<<<(unsigned)(blocks < 4096 ? blocks : 4096), 256, 0, s>>>(A.n, pp.ksel, mask, b);
+        k_bin_count<<<(unsigned)(blocks < 4096 ? blocks : 4096), 256, 0, s>>>(A.n, mask, b);
         count_launches(1);
     }
     k_bin_offsets<<<1, 32, 0, s>>>(b.ctr);
@@ -487,590 +480,6 @@ void launch_binning(const CscView& A, const PruneParams& pp, const ExpandBuffers
     if (A.n > 0) {
         k_bin_scatter<<<(unsigned)((A.n + 255) / 256), 256, 0, s>>>(A.n, b);
         count_launches(1);
-    }
-}
-
-// ---------------------------------------------------------------------------
-// the fused numeric kernel
-// ---------------------------------------------------------------------------
-
-struct ColShared {
-    BlockScratch bs;
-    int item;
-    int next;
-    int count;
-    int ovf;
-    int ncand;
-    int occ;
-    int cnt2;
-    int pad;
-};
-
-template <int H>
-struct HashCfg {
-    static constexpr int LOG2 = (H == 512) ? 9 : (H == 1024) ? 10 : (H == 2048) ? 11
-                              : (H == 4096) ? 12 : (H == 8192) ? 13 : 14;
-};
-
-// Insert (row, v) into the open-addressing table (linear probing).
-// Returns true when this call created the key.
-template <int H>
-__device__ __forceinline__ bool hash_add(uint64_t* table, int row, float v, int* ovf) {
-    unsigned h = ((unsigned)row * 0x9E3779B1u) >> (32 - HashCfg<H>::LOG2);
-    for (int probe = 0; probe < H; ++probe) {
-        int* kp = reinterpret_cast<int*>(table + h);
-        const int k = *reinterpret_cast<volatile int*>(kp);
-        if (k == row) {
-            atomicAdd(reinterpret_cast<float*>(kp) + 1, v);
-            return false;
-        }
-        if (k == -1) {
-            const int old = atomicCAS(kp, -1, row);
-            if (old == -1 || old == row) {
-                atomicAdd(reinterpret_cast<float*>(kp) + 1, v);
-                return old == -1;
-            }
-        }
-        h = (h + 1) & (H - 1);
-    }
-    *reinterpret_cast<volatile int*>(ovf) = 1;
-    return false;
-}
-
-__device__ __forceinline__ float inflate_value(float v, float r) {
-    if (r == 2.0f) return v * v;
-    if (r == 1.0f) return v;
-    return powf(v, r);
-}
-
-// Shared-memory layout of the numeric / prune kernels.
-template <int H, int T>
-struct NumLayout {
-    uint64_t* table;   // H slots: (int32 key | float value) or candidate keys
-    uint64_t* top;     // 2 * ksel ranking keys (ping-pong)
-    unsigned* hist;    // 256
-    double* mhist;     // 256
-    ColShared* cs;
-    __device__ NumLayout(unsigned char* smem, int ksel) {
-        table = reinterpret_cast<uint64_t*>(smem);
-        top = table + H;
-        hist = reinterpret_cast<unsigned*>(top + 2 * ksel);
-        mhist = reinterpret_cast<double*>(hist + 256);
-        cs = reinterpret_cast<ColShared*>(mhist + 256);
-    }
-    static size_t bytes(int ksel) {
-        return (size_t)H * 8 + (size_t)2 * ksel * 8 + 256 * 4 + 256 * 8 + sizeof(ColShared);
-    }
-};
-
-// Merge the c candidate keys in table[0..c) into the running top-ksel set
-// (top + which*ksel, ntop entries).  Updates ntop / which / tau uniformly
-// and leaves table[0..c) empty.
-template <int H, int T>
-__device__ __forceinline__ void merge_candidates(NumLayout<H, T>& L, int c, int ksel, int& ntop,
-                                                 int& which, uint64_t& tau, DevCounters* ctr) {
-    const int tid = threadIdx.x, lane = tid & 31;
-    if (c <= 0) return;
-    uint64_t* topA = L.top + which * ksel;
-    uint64_t* topB = L.top + (which ^ 1) * ksel;
-    if (ntop + c <= ksel) {
-        for (int i = tid; i < c; i += T) {
-            topA[ntop + i] = L.table[i];
-            L.table[i] = EMPTY_SLOT;
-        }
-        ntop += c;
-        __syncthreads();
-        return;
-    }
-    const uint64_t kap = block_select_count<T>(topA, ntop, L.table, c, ksel, L.hist, &L.cs->bs);
-    if (tid == 0) L.cs->cnt2 = 0;
-    __syncthreads();
-    const int tot = ntop + c;
-    for (int base = 0; base < tot; base += T) {
-        const int i = base + tid;
-        uint64_t x = 0;
-        bool keep = false;
-        if (i < tot) {
-            x = cat_at(topA, ntop, L.table, i);
-            keep = x >= kap;
-        }
-        const unsigned m = __ballot_sync(FULL, keep);
-        if (m) {
-            const int leader = __ffs(m) - 1;
-            int pos = 0;
-            if (lane == leader) pos = atomicAdd(&L.cs->cnt2, __popc(m));
-            pos = __shfl_sync(FULL, pos, leader);
-            const int at = pos + __popc(m & lanemask_lt());
-            if (keep) {
-                if (at < ksel) topB[at] = x;
-                else set_err(ctr, ERR_INTERNAL);
-            }
-        }
-    }
-    __syncthreads();
-    for (int i = tid; i < c; i += T) L.table[i] = EMPTY_SLOT;
-    if (tid == 0 && L.cs->cnt2 != ksel) set_err(ctr, ERR_INTERNAL);
-    ntop = ksel;
-    which ^= 1;
-    tau = kap;
-    __syncthreads();
-}
-
-// Finish a column from its top-ksel keys and exact statistics: decide m*
-// (prune rule), sort the kept entries by row, inflate + renormalise (FP64
-// sum) and compute chaos_j (FP64), write the column.
-template <int H, int T>
-__device__ __forceinline__ void finish_column(NumLayout<H, T>& L, const PruneParams& pp, int ntop,
-                                              int which, double S, double MT, long long Tt,
-                                              int64_t cap, int32_t* out_row, float* out_val,
-                                              int* mstar_out, double* chaos_out, DevCounters* ctr) {
-    const int tid = threadIdx.x, lane = tid & 31;
-    const int ksel = pp.ksel;
-    uint64_t* topA = L.top + which * ksel;
-    const double target = (double)pp.p * S;
-    const int q = (int)(Tt < (long long)pp.K ? Tt : (long long)pp.K);
-    double mq;
-    if (Tt <= pp.K) {
-        mq = MT;
-    } else {
-        const uint64_t kq = block_select_count<T>(topA, ntop, topA, 0, pp.K, L.hist, &L.cs->bs);
-        double part = 0.0;
-        for (int i = tid; i < ntop; i += T) {
-            const uint64_t x = topA[i];
-            if (x >= kq) part += (double)key_val(x);
-        }
-        double dv[1] = {part};
-        long long qv[1] = {0};
-        block_sum<T>(dv, 1, qv, 0, &L.cs->bs);
-        mq = dv[0];
-    }
-    int mstar;
-    if (target <= 0.0 || mq >= target) {
-        mstar = q;
-    } else {
-        uint64_t kr = 0;
-        int mr = 0;
-        const int f = block_select_mass<T>(topA, ntop, target, &kr, &mr, L.hist, L.mhist, &L.cs->bs);
-        mstar = f ? mr : ntop;
-    }
-    if (mstar > pp.Krec) mstar = pp.Krec;
-    if (mstar > ntop) mstar = ntop;
-    if ((int64_t)mstar > cap) {  // cannot happen for validated input; never write past cap
-        if (tid == 0) set_err(ctr, ERR_INTERNAL);
-        mstar = (int)cap;
-    }
-    uint64_t cut = 0;
-    if (mstar > 0 && mstar < ntop)
-        cut = block_select_count<T>(topA, ntop, topA, 0, mstar, L.hist, &L.cs->bs);
-    // kept entries -> sort records (row << 32 | value bits) in table[0..mstar)
-    if (tid == 0) L.cs->cnt2 = 0;
-    __syncthreads();
-    if (mstar > 0) {
-        for (int base = 0; base < ntop; base += T) {
-            const int i = base + tid;
-            uint64_t x = 0;
-            bool keep = false;
-            if (i < ntop) {
-                x = topA[i];
-                keep = x >= cut;
-            }
-            const unsigned m = __ballot_sync(FULL, keep);
-            if (m) {
-                const int leader = __ffs(m) - 1;
-                int pos = 0;
-                if (lane == leader) pos = atomicAdd(&L.cs->cnt2, __popc(m));
-                pos = __shfl_sync(FULL, pos, leader);
-                const int at = pos + __popc(m & lanemask_lt());
-                if (keep && at < H)
-                    L.table[at] = ((uint64_t)(uint32_t)key_row(x) << 32) | (uint32_t)(x >> 32);
-            }
-        }
-    }
-    __syncthreads();
-    const int P = next_pow2(mstar > 0 ? mstar : 1);
-    for (int i = mstar + tid; i < P; i += T) L.table[i] = ~0ull;
-    __syncthreads();
-    if (mstar > 1) block_bitonic_sort<T>(L.table, P);
-    // inflation + renormalisation
-    double usum = 0.0;
-    if (pp.inflate) {
-        for (int i = tid; i < mstar; i += T)
-            usum += (double)inflate_value(__uint_as_float((uint32_t)L.table[i]), pp.r);
-    }
-    double dv[1] = {usum};
-    long long qv[1] = {0};
-    block_sum<T>(dv, 1, qv, 0, &L.cs->bs);
-    const double U = dv[0];
-    double amax = 0.0, asq = 0.0;
-    for (int i = tid; i < mstar; i += T) {
-        const uint64_t rec = L.table[i];
-        const int row = (int)(rec >> 32);
-        const float v = __uint_as_float((uint32_t)rec);
-        float outv = v;
-        if (pp.inflate) {
-            const float u = inflate_value(v, pp.r);
-            const double a = U > 0.0 ? (double)u / U : 0.0;
-            outv = (float)a;
-            amax = a > amax ? a : amax;
-            asq += a * a;
-        }
-        out_row[i] = row;
-        out_val[i] = outv;
-    }
-    double ch = 0.0;
-    if (pp.inflate) {
-        const double mx = block_max_d<T>(amax, &L.cs->bs);
-        double dv2[1] = {asq};
-        block_sum<T>(dv2, 1, qv, 0, &L.cs->bs);
-        ch = mx - dv2[0];
-        if (ch < 0.0) ch = 0.0;
-    }
-    for (int i = tid; i < P; i += T) L.table[i] = EMPTY_SLOT;
-    if (tid == 0) {
-        *mstar_out = mstar;
-        *chaos_out = ch;
-    }
-    __syncthreads();
-}
-
-struct NumArgs {
-    CscView A;
-    PruneParams pp;
-    ExpandBuffers b;
-    int conf;
-};
-
-template <int H, int T>
-__global__ void __launch_bounds__(T) k_numeric(NumArgs a) {
-    static_assert(H * 3 / 4 + T <= H, "overflow limit must leave room for one chunk per warp");
-    constexpr int LIMIT = H * 3 / 4;
-    constexpr int IPR = 4;
-    extern __shared__ __align__(16) unsigned char smem[];
-    const int ksel = a.pp.ksel;
-    NumLayout<H, T> L(smem, ksel);
-    const int tid = threadIdx.x, lane = tid & 31;
-    const CscView& A = a.A;
-    const ExpandBuffers& b = a.b;
-    DevCounters* ctr = b.ctr;
-
-    for (int i = tid; i < H; i += T) L.table[i] = EMPTY_SLOT;
-    int32_t* cur = b.cursors + (int64_t)blockIdx.x * 2 * b.cur_stride;
-    int32_t* nxt = cur + b.cur_stride;
-    const int wbeg = ctr->bin_off[a.conf * NZ], wend = ctr->bin_off[a.conf * NZ + NZ];
-    __syncthreads();
-
-    for (;;) {
-        if (tid == 0) L.cs->item = atomicAdd(&ctr->conf_ctr[a.conf], 1);
-        __syncthreads();
-        const int item = L.cs->item;
-        __syncthreads();
-        if (wbeg + item >= wend) break;
-        const int j = b.work[wbeg + item];
-        const int64_t cb = A.colptr[j], ce = A.colptr[j + 1];
-        const int d = (int)(ce - cb);
-        const int lo = b.rlo[j], hiE = b.rhi[j] + 1;
-        const int64_t obase = b.off[j];
-        if (d == 0 || hiE <= lo) {
-            if (tid == 0) {
-                b.kept[j] = 0;
-                b.chaos[j] = 0.0;
-                b.bnnz[j] = 0;
-            }
-            continue;
-        }
-        if (d > b.cur_stride) {
-            if (tid == 0) {
-                set_err(ctr, ERR_CURSOR);
-                b.kept[j] = 0;
-                b.chaos[j] = 0.0;
-                b.bnnz[j] = 0;
-            }
-            continue;
-        }
-        const int span = hiE - lo;
-        int64_t est = b.est[j];
-        if (est < 1) est = 1;
-        int width;
-        if (span <= H) {
-            width = span;
-        } else {
-            const int64_t per = H / 2;
-            const int64_t R = (est + per - 1) / per;
-            width = (int)((span + R - 1) / R);
-            if (width < 1) width = 1;
-        }
-        for (int i = tid; i < d; i += T) cur[i] = 0;
-
-        int ntop = 0, which = 0;
-        uint64_t tau = 0;
-        double s_sum = 0.0, s_mt = 0.0;
-        long long s_t = 0, s_n = 0;
-        int r0 = lo;
-        __syncthreads();
-        while (r0 < hiE) {
-            const int r1 = (int)min((int64_t)r0 + width, (int64_t)hiE);
-            const bool dense = (r1 - r0) <= H;
-            if (tid == 0) {
-                L.cs->count = 0;
-                L.cs->ovf = 0;
-                L.cs->next = 0;
-                L.cs->ncand = 0;
-                L.cs->occ = 0;
-            }
-            __syncthreads();
-            // ---- accumulate the products with rows in [r0, r1) ----
-            for (;;) {
-                int kidx = 0;
-                if (lane == 0) kidx = atomicAdd(&L.cs->next, 1);
-                kidx = __shfl_sync(FULL, kidx, 0);
-                if (kidx >= d) break;
-                const int64_t pj = cb + kidx;
-                const int k = __ldg(A.rowidx + pj);
-                const float akj = __ldg(A.val + pj);
-                const int64_t ks = __ldg(A.colptr + k), ke = __ldg(A.colptr + k + 1);
-                int64_t pos = ks + cur[kidx];
-                while (pos < ke) {
-                    // warp-uniform read of the overflow flag (lane 0's view)
-                    int stop = lane == 0 ? *reinterpret_cast<volatile int*>(&L.cs->ovf) : 0;
-                    if (__shfl_sync(FULL, stop, 0)) break;
-                    const int64_t qq = pos + lane;
-                    const bool valid = qq < ke;
-                    const int rr = valid ? __ldg(A.rowidx + qq) : INT_MAX;
-                    const bool in = valid && rr < r1;
-                    const unsigned bal = __ballot_sync(FULL, in);
-                    bool created = false;
-                    if (in) {
-                        const float v = __ldg(A.val + qq) * akj;
-                        if (dense)
-                            atomicAdd(reinterpret_cast<float*>(L.table + (rr - r0)) + 1, v);
-                        else
-                            created = hash_add<H>(L.table, rr, v, &L.cs->ovf);
-                    }
-                    if (!dense) {
-                        const unsigned cm = __ballot_sync(FULL, created);
-                        if (cm && lane == 0) {
-                            const int tot = atomicAdd(&L.cs->count, __popc(cm)) + __popc(cm);
-                            if (tot > LIMIT) *reinterpret_cast<volatile int*>(&L.cs->ovf) = 1;
-                        }
-                    }
-                    const int nin = __popc(bal);
-                    pos += nin;
-                    if (nin < 32) break;
-                }
-                if (lane == 0) nxt[kidx] = (int)(pos - ks);
-            }
-            __syncthreads();
-            if (L.cs->ovf) {
-                for (int i = tid; i < H; i += T) L.table[i] = EMPTY_SLOT;
-                width = max((r1 - r0) / 2, 1);
-                if (tid == 0) atomicAdd(&ctr->splits, 1ull);
-                __syncthreads();
-                continue;
-            }
-            {
-                int32_t* t = cur;
-                cur = nxt;
-                nxt = t;
-            }
-            // ---- extract: statistics, ranking keys above tau -> table[0..c) ----
-            const int nslots = dense ? (r1 - r0) : H;
-            for (int base = 0; base < nslots; base += T * IPR) {
-                uint64_t kk[IPR];
-                int nocc = 0;
-#pragma unroll
-                for (int q = 0; q < IPR; ++q) {
-                    const int si = base + q * T + tid;
-                    kk[q] = 0;
-                    if (si < nslots) {
-                        const uint64_t sl = L.table[si];
-                        const float v = __uint_as_float((uint32_t)(sl >> 32));
-                        const int kr = (int)(uint32_t)sl;
-                        const bool occ = dense ? (v != 0.0f) : (kr != -1);
-                        if (occ) {
-                            const int row = dense ? (r0 + si) : kr;
-                            ++nocc;
-                            s_sum += (double)v;
-                            if (v >= a.pp.theta) {
-                                ++s_t;
-                                s_mt += (double)v;
-                            }
-                            const uint64_t key = make_key(v, row);
-                            if (key > tau) kk[q] = key;
-                            L.table[si] = EMPTY_SLOT;
-                        }
-                    }
-                }
-                s_n += nocc;
-                __syncthreads();
-#pragma unroll
-                for (int q = 0; q < IPR; ++q) {
-                    const bool has = kk[q] != 0;
-                    const unsigned m = __ballot_sync(FULL, has);
-                    if (m) {
-                        const int leader = __ffs(m) - 1;
-                        int pos = 0;
-                        if (lane == leader) pos = atomicAdd(&L.cs->ncand, __popc(m));
-                        pos = __shfl_sync(FULL, pos, leader);
-                        const int at = pos + __popc(m & lanemask_lt());
-                        if (has && at < H) L.table[at] = kk[q];
-                    }
-                }
-                const int wocc = warp_sum(nocc);
-                if (lane == 0 && wocc) atomicAdd(&L.cs->occ, wocc);
-            }
-            __syncthreads();
-            const int c = L.cs->ncand;
-            const int occ = L.cs->occ;
-            merge_candidates<H, T>(L, c, ksel, ntop, which, tau, ctr);
-            r0 = r1;
-            if (occ * 4 < H && width < span) width = (int)min((int64_t)width * 2, (int64_t)span);
-        }
-        double dv[2] = {s_sum, s_mt};
-        long long qv[2] = {s_t, s_n};
-        block_sum<T>(dv, 2, qv, 2, &L.cs->bs);
-        int mstar = 0;
-        double ch = 0.0;
-        finish_column<H, T>(L, a.pp, ntop, which, dv[0], dv[1], qv[0], b.cap[j],
-                            b.tmp_row + obase, b.tmp_val + obase, &mstar, &ch, ctr);
-        if (tid == 0) {
-            b.kept[j] = mstar;
-            b.chaos[j] = ch;
-            b.bnnz[j] = qv[1];
-            if (qv[1] > est) atomicAdd(&ctr->misses, 1ull);
-        }
-    }
-}
-
-template <int H, int T>
-static void set_numeric_attr(size_t smem) {
-    cudaFuncSetAttribute(k_numeric<H, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-}
-
-size_t numeric_smem(int conf, int ksel) {
-    switch (conf) {
-        case 0: return NumLayout<512, 128>::bytes(ksel);
-        case 1: return NumLayout<2048, 256>::bytes(ksel);
-        case 2: return NumLayout<8192, 512>::bytes(ksel);
-        default: return NumLayout<16384, 1024>::bytes(ksel);
-    }
-}
-
-int numeric_grid(int conf, int ksel, int num_sms) {
-    size_t smem = numeric_smem(conf, ksel);
-    int occ = 0;
-    switch (conf) {
-        case 0:
-            set_numeric_attr<512, 128>(smem);
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_numeric<512, 128>, 128, smem);
-            break;
-        case 1:
-            set_numeric_attr<2048, 256>(smem);
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_numeric<2048, 256>, 256, smem);
-            break;
-        case 2:
-            set_numeric_attr<8192, 512>(smem);
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_numeric<8192, 512>, 512, smem);
-            break;
-        default:
-            set_numeric_attr<16384, 1024>(smem);
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_numeric<16384, 1024>, 1024, smem);
-            break;
-    }
-    if (occ < 1) occ = 1;
-    return occ * num_sms;
-}
-
-void launch_numeric(int conf, const CscView& A, const PruneParams& pp, const ExpandBuffers& b,
-                    int grid, cudaStream_t s) {
-    NumArgs a{A, pp, b, conf};
-    size_t smem = numeric_smem(conf, pp.ksel);
-    switch (conf) {
-        case 0: k_numeric<512, 128><<<grid, 128, smem, s>>>(a); break;
-        case 1: k_numeric<2048, 256><<<grid, 256, smem, s>>>(a); break;
-        case 2: k_numeric<8192, 512><<<grid, 512, smem, s>>>(a); break;
-        default: k_numeric<16384, 1024><<<grid, 1024, smem, s>>>(a); break;
-    }
-    count_launches(1);
-}
-
-// ---------------------------------------------------------------------------
-// the prune rule alone on a materialised matrix
-// ---------------------------------------------------------------------------
-
-constexpr int PR_H = 4096, PR_T = 256;
-
-struct PruneArgs {
-    CscView B;
-    PruneParams pp;
-    ExpandBuffers b;
-};
-
-__global__ void __launch_bounds__(PR_T) k_prune(PruneArgs a) {
-    extern __shared__ __align__(16) unsigned char smem[];
-    const int ksel = a.pp.ksel;
-    NumLayout<PR_H, PR_T> L(smem, ksel);
-    const int tid = threadIdx.x, lane = tid & 31;
-    const CscView& B = a.B;
-    const ExpandBuffers& b = a.b;
-    for (int i = tid; i < PR_H; i += PR_T) L.table[i] = EMPTY_SLOT;
-    __syncthreads();
-    for (;;) {
-        if (tid == 0) L.cs->item = atomicAdd(&b.ctr->work_ctr, 1);
-        __syncthreads();
-        const int64_t j = L.cs->item;
-        __syncthreads();
-        if (j >= B.n) break;
-        const int64_t cb = B.colptr[j], ce = B.colptr[j + 1];
-        int ntop = 0, which = 0;
-        uint64_t tau = 0;
-        double s_sum = 0.0, s_mt = 0.0;
-        long long s_t = 0;
-        for (int64_t base = cb; base < ce; base += PR_H) {
-            const int cnt = (int)min((int64_t)PR_H, ce - base);
-            if (tid == 0) L.cs->ncand = 0;
-            __syncthreads();
-            for (int o = 0; o < cnt; o += PR_T) {
-                const int i = o + tid;
-                uint64_t key = 0;
-                if (i < cnt) {
-                    const float v = B.val[base + i];
-                    const int row = B.rowidx[base + i];
-                    s_sum += (double)v;
-                    if (v >= a.pp.theta) {
-                        ++s_t;
-                        s_mt += (double)v;
-                    }
-                    const uint64_t k = make_key(v, row);
-                    if (k > tau) key = k;
-                }
-                const bool has = key != 0;
-                const unsigned m = __ballot_sync(FULL, has);
-                if (m) {
-                    const int leader = __ffs(m) - 1;
-                    int pos = 0;
-                    if (lane == leader) pos = atomicAdd(&L.cs->ncand, __popc(m));
-                    pos = __shfl_sync(FULL, pos, leader);
-                    const int at = pos + __popc(m & lanemask_lt());
-                    if (has && at < PR_H) L.table[at] = key;
-                }
-            }
-            __syncthreads();
-            const int c = L.cs->ncand;
-            merge_candidates<PR_H, PR_T>(L, c, ksel, ntop, which, tau, b.ctr);
-        }
-        double dv[2] = {s_sum, s_mt};
-        long long qv[1] = {s_t};
-        block_sum<PR_T>(dv, 2, qv, 1, &L.cs->bs);
-        int mstar = 0;
-        double ch = 0.0;
-        const int64_t obase = b.off[j];
-        finish_column<PR_H, PR_T>(L, a.pp, ntop, which, dv[0], dv[1], qv[0], b.cap[j],
-                                  b.tmp_row + obase, b.tmp_val + obase, &mstar, &ch, b.ctr);
-        if (tid == 0) {
-            b.kept[j] = mstar;
-            b.chaos[j] = ch;
-            b.bnnz[j] = ce - cb;
-        }
     }
 }
 
@@ -1085,21 +494,6 @@ __global__ void k_prune_cap(CscView B, int32_t Krec, ExpandBuffers b) {
 void launch_prune_cap(const CscView& B, int32_t Krec, const ExpandBuffers& b, cudaStream_t s) {
     if (B.n == 0) return;
     k_prune_cap<<<(unsigned)((B.n + 255) / 256), 256, 0, s>>>(B, Krec, b);
-    count_launches(1);
-}
-
-void launch_prune(const CscView& B, const PruneParams& pp, const ExpandBuffers& b, int num_sms,
-                  cudaStream_t s) {
-    if (B.n == 0) return;
-    size_t smem = NumLayout<PR_H, PR_T>::bytes(pp.ksel);
-    cudaFuncSetAttribute(k_prune, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    int occ = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_prune, PR_T, smem);
-    if (occ < 1) occ = 1;
-    int grid = occ * num_sms;
-    if ((int64_t)grid > B.n) grid = (int)B.n;
-    cudaMemsetAsync(&b.ctr->work_ctr, 0, sizeof(int), s);
-    k_prune<<<grid, PR_T, smem, s>>>(PruneArgs{B, pp, b});
     count_launches(1);
 }
 
