@@ -30,7 +30,8 @@ struct mcl_ctx {
     char err[512] = {0};
     // scratch
     Buf flops, rlo, rhi, cap, off, est, bucket, work, kept, chaos, bnnz, tmp_row, tmp_val,
-        cursors, scan, ctr, active, bucket_row, bucket_val, woff;
+        cursors, scan, ctr, active, bucket_row, bucket_val, woff, comp_off, comp_of_col,
+        comp_bits, comp_active;
     size_t bucket_budget = (size_t)32 << 30;  // bytes of product buckets (large config)
     DevCounters* hctr = nullptr;  // pinned host mirror
     mcl_stats stats{};
@@ -266,7 +267,8 @@ void mcl_destroy(mcl_ctx* c) {
     if (!c) return;
     cudaSetDevice(c->device);
     cudaDeviceSynchronize();
-    Buf* all[] = {&c->bucket_row, &c->bucket_val, &c->woff,
+    Buf* all[] = {&c->bucket_row, &c->bucket_val, &c->woff, &c->comp_off, &c->comp_of_col,
+                  &c->comp_bits, &c->comp_active,
                   &c->flops, &c->rlo,     &c->rhi,     &c->cap,     &c->off,  &c->est,
                   &c->bucket, &c->work,   &c->kept,    &c->chaos,   &c->bnnz, &c->tmp_row,
                   &c->tmp_val, &c->cursors, &c->scan,  &c->ctr,     &c->active, &c->mlp_w,
@@ -399,10 +401,7 @@ static mcl_status expand_impl(mcl_ctx* c, const mcl_csc* A, const mcl_params* pr
     // ---- output ----
     int64_t* colptr_out = (int64_t*)dev_alloc(c, (size_t)(n + 1) * 8, s);
     if (!colptr_out) return fail(c, MCL_ERR_OOM, "output colptr allocation failed");
-    if (active) {
-        // inactive columns keep their input length
-        return fail(c, MCL_ERR_INTERNAL, "active mask requires mcl_run");
-    }
+    if (active) launch_fill_inactive(Av, active, b.kept, s);  // carried columns keep their length
     launch_exclusive_scan<int32_t>(b.kept, n, colptr_out, b.scan_tmp, &b.ctr->nnz_out, s);
     if ((st = check_launch(c, "scan"))) {
         dev_free(c, colptr_out, s);
@@ -689,6 +688,33 @@ mcl_status mcl_run(mcl_ctx* c, const mcl_csc* A0, const int32_t* comp_offsets, i
     if (A0->n > 0 && !labels) return fail(c, MCL_ERR_INVALID, "labels is NULL");
     if (comp_offsets && ncomp < 1) return fail(c, MCL_ERR_INVALID, "ncomp must be >= 1");
     cudaStream_t s = (cudaStream_t)stream;
+    const bool batched = comp_offsets && prm->batched;
+    if (batched) {
+        if (comp_offsets[0] != 0 || comp_offsets[ncomp] != A0->n)
+            return fail(c, MCL_ERR_INVALID, "comp_offsets must run from 0 to n");
+        for (int q = 0; q < ncomp; ++q)
+            if (comp_offsets[q + 1] < comp_offsets[q])
+                return fail(c, MCL_ERR_INVALID, "comp_offsets must be nondecreasing");
+        CUDA_TRY(c, cudaSetDevice(c->device));
+        const size_t n1 = (size_t)A0->n + 1;
+        if (!ensure(c, c->comp_off, (size_t)(ncomp + 1) * 4, s) ||
+            !ensure(c, c->comp_of_col, n1 * 4, s) || !ensure(c, c->comp_bits, (size_t)ncomp * 8, s) ||
+            !ensure(c, c->comp_active, (size_t)ncomp, s) || !ensure(c, c->active, n1, s) ||
+            !ensure(c, c->ctr, sizeof(DevCounters), s))
+            return fail(c, MCL_ERR_OOM, "batch scratch allocation failed");
+        CUDA_TRY(c, cudaMemcpyAsync(c->comp_off.p, comp_offsets, (size_t)(ncomp + 1) * 4,
+                                    cudaMemcpyHostToDevice, s));
+        CUDA_TRY(c, cudaMemsetAsync(c->ctr.p, 0, sizeof(DevCounters), s));
+        launch_comp_assign(view(A0), (const int32_t*)c->comp_off.p, ncomp,
+                           (int32_t*)c->comp_of_col.p, (DevCounters*)c->ctr.p, s);
+        if ((st = read_counters(c, s))) return st;
+        if (c->hctr->err & ERR_ROW_RANGE)
+            return fail(c, MCL_ERR_INVALID, "A0 is not block diagonal over comp_offsets");
+        CUDA_TRY(c, cudaMemsetAsync(c->comp_active.p, 1, (size_t)ncomp, s));
+    }
+    std::vector<unsigned long long> hbits(batched ? ncomp : 0);
+    std::vector<uint8_t> hact(batched ? ncomp : 0, 1);
+    int nactive = batched ? ncomp : 1;
     mcl_csc cur = *A0;
     bool owned = false;
     int it = 0;
@@ -699,7 +725,33 @@ mcl_status mcl_run(mcl_ctx* c, const mcl_csc* A0, const int32_t* comp_offsets, i
     while (it < prm->max_iters) {
         mcl_csc nxt{};
         c->iteration = it + 1;
-        st = expand_impl(c, &cur, prm, &nxt, &ch, s, nullptr);
+        const uint8_t* act = nullptr;
+        if (batched) {
+            launch_active_from_comp(cur.n, (const int32_t*)c->comp_of_col.p,
+                                    (const uint8_t*)c->comp_active.p, (uint8_t*)c->active.p, s);
+            act = (const uint8_t*)c->active.p;
+        }
+        st = expand_impl(c, &cur, prm, &nxt, &ch, s, act);
+        if (!st && batched) {
+            // per-component chaos of this iteration; converged components retire
+            cudaMemsetAsync(c->comp_bits.p, 0, (size_t)ncomp * 8, s);
+            launch_comp_chaos(cur.n, (const int32_t*)c->comp_of_col.p, act,
+                              (const double*)c->chaos.p, (unsigned long long*)c->comp_bits.p, s);
+            cudaMemcpyAsync(hbits.data(), c->comp_bits.p, (size_t)ncomp * 8, cudaMemcpyDeviceToHost,
+                            s);
+            if (cudaStreamSynchronize(s) != cudaSuccess)
+                st = fail(c, MCL_ERR_CUDA, "component chaos readback failed");
+            nactive = 0;
+            for (int q = 0; q < ncomp && !st; ++q) {
+                if (!hact[q]) continue;
+                if (chaos_from_bits(hbits[q]) < prm->chaos_eps)
+                    hact[q] = 0;
+                else
+                    ++nactive;
+            }
+            if (!st)
+                cudaMemcpyAsync(c->comp_active.p, hact.data(), (size_t)ncomp, cudaMemcpyHostToDevice, s);
+        }
         if (!st && prm->use_estimator) {
             // the compression factor of this iteration feeds the next one's features
             if (ensure(c, c->prev_logcf, ((size_t)cur.n + 1) * 4, s)) {
@@ -719,7 +771,7 @@ mcl_status mcl_run(mcl_ctx* c, const mcl_csc* A0, const int32_t* comp_offsets, i
         owned = true;
         if (chaos_hist) chaos_hist[it] = ch;
         ++it;
-        if (ch < prm->chaos_eps) {
+        if (batched ? nactive == 0 : ch < prm->chaos_eps) {
             converged = true;
             break;
         }

@@ -123,6 +123,13 @@ void launch_inflate_normalize(int32_t n, const int64_t* colptr, float* val, floa
 void launch_chaos(int32_t n, const int64_t* colptr, const float* val, double* chaos_cols,
                   DevCounters* ctr, cudaStream_t s);
 void launch_fill_colptr(int32_t n, int64_t* colptr, cudaStream_t s);
+void launch_comp_assign(const CscView& A, const int32_t* off, int32_t ncomp, int32_t* comp_of_col,
+                        DevCounters* ctr, cudaStream_t s);
+void launch_active_from_comp(int32_t n, const int32_t* comp_of_col, const uint8_t* comp_active,
+                             uint8_t* active, cudaStream_t s);
+void launch_fill_inactive(const CscView& A, const uint8_t* active, int32_t* kept, cudaStream_t s);
+void launch_comp_chaos(int32_t n, const int32_t* comp_of_col, const uint8_t* active,
+                       const double* chaos, unsigned long long* comp_bits, cudaStream_t s);
 
 // --- estimator (mcl_estimator.cu) ---
 void launch_colmax_features(const CscView& A, int32_t iteration, const float* prev_logcf,

@@ -637,6 +637,95 @@ void launch_chaos(int32_t n, const int64_t* colptr, const float* val, double* ch
     count_launches(1);
 }
 
+// ---------------------------------------------------------------------------
+// batched components: per-column component, active mask, per-component chaos
+// ---------------------------------------------------------------------------
+
+// comp_of_col[j] = c with off[c] <= j < off[c+1] (binary search); flags a
+// column whose rows leave its component (the batch must be block diagonal).
+__global__ void k_comp_assign(CscView A, const int32_t* off, int32_t ncomp, int32_t* comp_of_col,
+                              DevCounters* ctr) {
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= A.n) return;
+    int lo = 0, hi = ncomp;  // invariant: off[lo] <= j < off[hi]
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (off[mid] <= j) lo = mid; else hi = mid;
+    }
+    comp_of_col[j] = lo;
+    const int64_t cb = A.colptr[j], ce = A.colptr[j + 1];
+    if (ce > cb) {
+        const int r0 = A.rowidx[cb], r1 = A.rowidx[ce - 1];
+        if (r0 < off[lo] || r1 >= off[lo + 1]) atomicOr(&ctr->err, ERR_ROW_RANGE);
+    }
+}
+
+__global__ void k_active_from_comp(int32_t n, const int32_t* comp_of_col, const uint8_t* comp_active,
+                                   uint8_t* active) {
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < n) active[j] = comp_active[comp_of_col[j]];
+}
+
+// kept count of a carried (inactive) column = its input length
+__global__ void k_fill_inactive(CscView A, const uint8_t* active, int32_t* kept) {
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < A.n && !active[j]) kept[j] = (int32_t)(A.colptr[j + 1] - A.colptr[j]);
+}
+
+// max chaos_j per component over its active columns (ordered bits, >= 0);
+// the lanes of a warp are grouped by component, one atomic per group
+__global__ void k_comp_chaos(int32_t n, const int32_t* comp_of_col, const uint8_t* active,
+                             const double* chaos, unsigned long long* comp_bits) {
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    const bool valid = j < n && active[j];
+    const int c = valid ? comp_of_col[j] : -1;
+    const unsigned long long bits = valid ? (unsigned long long)__double_as_longlong(chaos[j]) : 0ull;
+    unsigned rem = __ballot_sync(FULL, valid);
+    while (rem) {
+        const int leader = __ffs(rem) - 1;
+        const int cl = __shfl_sync(FULL, c, leader);
+        const bool mine = valid && c == cl;
+        unsigned long long v = mine ? bits : 0ull;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long y = __shfl_xor_sync(FULL, v, o);
+            v = y > v ? y : v;
+        }
+        if (lane == leader) atomicMax(comp_bits + cl, v);
+        rem &= ~__ballot_sync(FULL, mine);
+    }
+}
+
+void launch_comp_assign(const CscView& A, const int32_t* off, int32_t ncomp, int32_t* comp_of_col,
+                        DevCounters* ctr, cudaStream_t s) {
+    if (A.n == 0) return;
+    k_comp_assign<<<(unsigned)((A.n + 255) / 256), 256, 0, s>>>(A, off, ncomp, comp_of_col, ctr);
+    count_launches(1);
+}
+
+void launch_active_from_comp(int32_t n, const int32_t* comp_of_col, const uint8_t* comp_active,
+                             uint8_t* active, cudaStream_t s) {
+    if (n == 0) return;
+    k_active_from_comp<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, comp_of_col, comp_active,
+                                                                    active);
+    count_launches(1);
+}
+
+void launch_fill_inactive(const CscView& A, const uint8_t* active, int32_t* kept, cudaStream_t s) {
+    if (A.n == 0) return;
+    k_fill_inactive<<<(unsigned)((A.n + 255) / 256), 256, 0, s>>>(A, active, kept);
+    count_launches(1);
+}
+
+void launch_comp_chaos(int32_t n, const int32_t* comp_of_col, const uint8_t* active,
+                       const double* chaos, unsigned long long* comp_bits, cudaStream_t s) {
+    if (n == 0) return;
+    k_comp_chaos<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, comp_of_col, active, chaos,
+                                                              comp_bits);
+    count_launches(1);
+}
+
 __global__ void k_fill_colptr(int32_t n, int64_t* colptr) {
     int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (j <= n) colptr[j] = 0;

@@ -298,3 +298,40 @@ def test_zipf1m_one_iteration_sampled(ctx, zipf1m):
     assert rep.ok(), rep.failures[:5]
     st = ctx.stats()
     assert st["flops"] == int((deg.astype(np.int64) ** 2).sum())
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_batched_components_match_per_component_runs(ctx, seed):
+    """Batched MCL over independent components (each stops on its own chaos)
+    equals running every component separately, on the GPU and in the
+    oracle."""
+    from paper_2002_10083_gb300 import mcl
+    A = synth.component_batch(ncomp=24, size_lo=50, size_hi=1500, p_in=0.3, p_out=0.002,
+                              seed=seed).with_val32()
+    offs = A.comp_offsets
+    prm = _prm(theta=1e-4, K=200, p=0.9, iters=40)
+    prm.batched = 1
+    lab, iters, hist, final, notconv = ctx.run(_dev(A), prm, comp_offsets=offs)
+    assert not notconv
+    lab = lab.cpu().numpy()
+    # oracle, per component
+    _, o_iters, _, o_lab = oracle.run_mcl(A, _oprm(prm), per_component=offs)
+    assert iters == max(o_iters)
+    assert np.array_equal(lab, o_lab)
+    # GPU, per component, one run each
+    prm1 = _prm(theta=1e-4, K=200, p=0.9, iters=40)
+    for c in range(len(offs) - 1):
+        sub = oracle.submatrix(A, int(offs[c]), int(offs[c + 1]))
+        l1, it1, _, _, nc1 = ctx.run(_dev(sub), prm1, keep_final=False)
+        assert it1 == o_iters[c]
+        assert np.array_equal(l1.cpu().numpy() + offs[c], lab[offs[c]:offs[c + 1]])
+
+
+def test_batched_rejects_non_block_diagonal(ctx):
+    from paper_2002_10083_gb300 import mcl
+    A = synth.random_sparse(100, 0.05, seed=1)
+    prm = _prm()
+    prm.batched = 1
+    with pytest.raises(mcl.MclError) as ei:
+        ctx.run(_dev(A), prm, comp_offsets=np.array([0, 50, 100], np.int32))
+    assert ei.value.status == 1
