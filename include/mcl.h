@@ -276,6 +276,35 @@ mcl_status mcl_estimate(mcl_ctx* ctx, const mcl_csc* A, int64_t* est, void* stre
 /* Statistics of the last mcl_expand / mcl_run on ctx. */
 mcl_status mcl_get_stats(mcl_ctx* ctx, mcl_stats* stats);
 
+/*
+ * Allocation-free exact symbolic pass (the paper has no counterpart; it is
+ * an interface for callers that cannot allocate device memory where they
+ * need output sizes -- e.g. a service that reserves all of its GPU memory
+ * in a pool at start-up and forbids allocation afterwards, because
+ * cudaMalloc can synchronise the device and fail under fragmentation).
+ *
+ * Computes what mcl_symbolic computes -- flops_j and nnz((AA)_*j), device
+ * int64[n] outputs supplied by the caller (either may be NULL, not both) --
+ * without a context and without allocating: no cudaMalloc / cudaFree and no
+ * allocator callback.  Its scratch is one file-scope device array of
+ * MCL_NOALLOC_SCRATCH_BYTES (64 MiB), which every GPU that loads this
+ * library holds until the process exits.  It needs 24 bytes per column
+ * (so n up to about 2.79 million) plus cursor space for the longest
+ * column; larger inputs are rejected with MCL_ERR_INVALID and a message in
+ * errbuf (caller memory of errlen bytes, may be NULL).
+ *
+ * The first call on a device looks up the array's device address (with
+ * that device current) and caches it; make that first call before any
+ * stream capture.  Every call shares the one array, which keeps the last
+ * call's contents (the call clears what must start at zero): calls that
+ * overlap on the GPU -- on different streams or host threads -- race and
+ * must be serialised by the caller.  Synchronises `stream` once (after the
+ * column statistics, to check them and size the cursors).
+ */
+#define MCL_NOALLOC_SCRATCH_BYTES (64 * 1024 * 1024)
+mcl_status mcl_symbolic_noalloc(const mcl_csc* A, int64_t* flops, int64_t* nnz_out, char* errbuf,
+                                size_t errlen, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -86,6 +86,8 @@ SIGNATURES = {
     "mcl_adam_step": (ctypes.c_int, [P, P, P, P, P, ctypes.c_int64, ctypes.c_float, ctypes.c_float,
                                      ctypes.c_float, ctypes.c_float, P, P]),
     "mcl_estimate": (ctypes.c_int, [P, ctypes.POINTER(_Csc), P, P]),
+    "mcl_symbolic_noalloc": (ctypes.c_int, [ctypes.POINTER(_Csc), P, P, ctypes.c_char_p,
+                                            ctypes.c_size_t, P]),
 }
 MLP_NPARAM = 5378
 NFEATURES = 16
@@ -97,6 +99,20 @@ _lib_lock = threading.Lock()
 def launch_count() -> int:
     """Kernels launched by libmcl.so in this process so far."""
     return int(load().mcl_launch_count())
+
+
+def symbolic_noalloc(A: "DeviceCSC", flops=None, nnz_out=None, stream=None):
+    """mcl_symbolic_noalloc: flops_j and nnz((AA)_*j) into caller-allocated
+    int64 device tensors, with no context and no allocation in the library."""
+    lib = load()
+    a = A.c()
+    err = ctypes.create_string_buffer(512)
+    st = lib.mcl_symbolic_noalloc(ctypes.byref(a),
+                                  P(flops.data_ptr()) if flops is not None else None,
+                                  P(nnz_out.data_ptr()) if nnz_out is not None else None,
+                                  err, len(err), _stream_ptr(stream))
+    if st != MCL_OK:
+        raise MclError(st, err.value.decode())
 
 
 def library_path() -> str:
