@@ -171,6 +171,23 @@ def run_reference(args):
     return 0
 
 
+def _time_form(ctx, D, prm, steps, stream, torch, mcl):
+    """Time `steps` mcl_expand calls; returns (ms per step, median numeric ms, stats)."""
+    ms_num = []
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    st = None
+    for _ in range(steps):
+        out, ch = ctx.expand(D, prm)
+        st = ctx.stats()
+        ms_num.append(st["ms_numeric"])
+        del out
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps, statistics.median(ms_num), st
+
+
 def run_gpu(args):
     import torch
     rank, local, world = _env_rank()
@@ -180,25 +197,25 @@ def run_gpu(args):
         dist = dist_
         torch.cuda.set_device(local)
         dist.init_process_group("nccl")
-    from paper_2002_10083_gb300 import mcl
+    from paper_2002_10083_gb300 import estimator, mcl
     dev = local
     torch.cuda.set_device(dev)
     A = make_workload(args.workload, n=args.n)
     n, nnz = A.n, A.nnz
     D = mcl.DeviceCSC.from_host(A, device=f"cuda:{dev}")
     ctx = mcl.Context(dev)
-    if args.sizing is not None:
-        ctx.set_option(mcl.OPT_SIZING, {"exact": 0, "flops": 1}[args.sizing])
-    prm = mcl.Params(**PARAMS)
+    meta = estimator.install(ctx)
+    prm_plain = mcl.Params(**PARAMS)
+    prm_learn = mcl.Params(**PARAMS, use_estimator=1)
+    prm_main = prm_plain if args.form == "plain" else prm_learn
     stream = torch.cuda.current_stream()
 
-    # warm-up
+    # warm-up (both forms)
     for _ in range(args.warmup):
-        out, ch = ctx.expand(D, prm)
-        del out
+        for prm in (prm_plain, prm_learn):
+            out, ch = ctx.expand(D, prm)
+            del out
     torch.cuda.synchronize()
-    st = ctx.stats()
-    flops = int(st["flops"])
 
     # timed region: device-resident inputs (A is ~400 MB, larger than L2)
     gpu_idx = os.environ.get("CUDA_VISIBLE_DEVICES", str(dev)).split(",")[dev if world == 1 else local]
@@ -210,28 +227,21 @@ def run_gpu(args):
         clk.start()
         time.sleep(0.3)
     l0 = mcl.launch_count()
-    ms_num, nnz_out, nnz_b, ms_tot = [], 0, 0, []
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(args.steps):
-        out, ch = ctx.expand(D, prm)
-        s = ctx.stats()
-        ms_num.append(s["ms_numeric"])
-        ms_tot.append(s["ms_total"])
-        nnz_out, nnz_b = int(s["nnz_out"]), int(s["nnz_b"])
-        del out
-    e1.record(stream)
+    ms, t_num, st = _time_form(ctx, D, prm_main, args.steps, stream, torch, mcl)
+    launches = mcl.launch_count() - l0
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
-    launches = mcl.launch_count() - l0
     clocks = clk.stop() if clk else None
-    ms = e0.elapsed_time(e1) / args.steps
     if dist:
         t = torch.tensor([ms], device=f"cuda:{dev}")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
+    flops = int(st["flops"])
+    nnz_out, nnz_b = int(st["nnz_out"]), int(st["nnz_b"])
+    # the other form, same workload, for the comparison the metric asks for
+    other = prm_plain if prm_main is prm_learn else prm_learn
+    ms_o, t_num_o, st_o = _time_form(ctx, D, other, args.steps, stream, torch, mcl)
 
     # end to end through the C ABI with host buffers (pinned): H2D of A,
     # the iteration, D2H of the resulting matrix
@@ -246,7 +256,7 @@ def run_gpu(args):
         Dh = mcl.DeviceCSC(n, hcp.to(f"cuda:{dev}", non_blocking=True),
                            hri.to(f"cuda:{dev}", non_blocking=True),
                            hva.to(f"cuda:{dev}", non_blocking=True))
-        out, ch = ctx.expand(Dh, prm)
+        out, ch = ctx.expand(Dh, prm_main)
         ocp = torch.empty(out.colptr.shape, dtype=torch.int64, pin_memory=True)
         ori = torch.empty(out.rowidx.shape, dtype=torch.int32, pin_memory=True)
         ova = torch.empty(out.val.shape, dtype=torch.float32, pin_memory=True)
@@ -264,7 +274,6 @@ def run_gpu(args):
     gflops = 2.0 * flops / (ms / 1000.0) / 1e9 * world
     e2e_gflops = 2.0 * flops / (e2e_ms / 1000.0) / 1e9 * world if e2e_steps else None
     peak, peak_kind = _peaks()
-    t_num = statistics.median(ms_num)
     b_alg = 8 * nnz + 8 * flops + 8 * nnz_out + 16 * n
     achieved = b_alg / (t_num / 1000.0) / 1e9
     cpu = None
@@ -272,6 +281,15 @@ def run_gpu(args):
         g, dt, ncols, cores = oracle_gflops(A, args.cpu_seconds)
         cpu = {"value": round(g, 4), "unit": "GFLOP/s", "cores": cores, "kind": "oracle",
                "sample": f"{ncols} random columns of the same workload ({dt:.1f} s)"}
+    main_name = "learned" if prm_main is prm_learn else "plain"
+    other_name = "plain" if main_name == "learned" else "learned"
+
+    def form_line(msv, tnum, s):
+        return {"value": round(2.0 * flops / (msv / 1000.0) / 1e9 * world, 2), "unit": "GFLOP/s",
+                "ms_per_step": round(msv, 3), "iters_per_s": round(1000.0 / msv, 4),
+                "numeric_ms": round(tnum, 3), "estimate_ms": round(s["ms_estimate"], 3),
+                "estimator_misses": int(s["estimator_misses"]), "window_cuts": int(s["range_splits"])}
+
     line = {
         "metric": METRIC, "value": round(gflops, 2), "unit": "GFLOP/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 3),
@@ -279,13 +297,19 @@ def run_gpu(args):
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "n": n, "nnz": nnz, "flops_per_step": flops,
                    "nnz_b": nnz_b, "nnz_out": nnz_out,
-                   "form": args.sizing or "plain (exact symbolic sizing)",
+                   "form": main_name + (" (MLP sizing; estimator trained on seeds %s, held-out "
+                                        "median |log ratio| %.4f)" % (
+                                            "1-20", meta.get("eval", {}).get("median_abs_log_ratio", -1))
+                                        if main_name == "learned" else " (exact symbolic sizing)"),
                    "l2": "inputs larger than L2 (A is %.0f MB)" % (in_bytes / 1e6),
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "iters_per_s": round(world * 1000.0 / ms, 3),
+        main_name: form_line(ms, t_num, st),
+        other_name: form_line(ms_o, t_num_o, st_o),
+        "speedup_learned_vs_plain": round((ms_o / ms) if main_name == "learned" else (ms / ms_o), 4),
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 4), "traffic": None,
-                     "kernel": "k_numeric (all accumulator configurations of one step)",
+                     "kernel": "k_expand (numeric pass, both configurations, one step)",
                      "algorithmic_bytes": b_alg, "kernel_ms": round(t_num, 3),
                      "peak_kind": peak_kind},
         "cpu_baseline": cpu,
@@ -294,7 +318,7 @@ def run_gpu(args):
                 if e2e_steps else None),
         "gpu_launches": int(launches),
         "clocks": clocks,
-        "stage_ms": {k: round(v, 3) for k, v in ctx.stats().items() if k.startswith("ms_")},
+        "stage_ms": {k: round(v, 3) for k, v in st.items() if k.startswith("ms_")},
     }
     print(json.dumps(line), flush=True)
     ctx.close()
@@ -310,7 +334,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="zipf1m")
-    ap.add_argument("--sizing", default=None, choices=[None, "exact", "flops"])
+    ap.add_argument("--form", default="learned", choices=["learned", "plain"])
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")

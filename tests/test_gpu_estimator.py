@@ -144,3 +144,45 @@ def test_learned_sizing_same_results(trained, ctx):
     lab_l, it_l, h_l, _, _ = ctx.run(_dev(A), prm_learn, keep_final=False)
     assert it_p == it_l
     np.testing.assert_allclose(h_l, h_p, rtol=1e-4, atol=1e-7)
+
+
+@pytest.mark.slow
+def test_trained_estimator_gain_on_held_out_graph(ctx):
+    """The committed estimator (trained on seeds 1-20) on the held-out
+    1M-vertex graph seed 100: its estimates are within a few percent of the
+    exact symbolic counts, the learned form replaces the symbolic pass and
+    is faster than the plain form, and its results match the oracle."""
+    import time
+    from paper_2002_10083_gb300 import estimator, mcl
+    meta = estimator.install(ctx)
+    A = synth.config("zipf1m", seed=100).with_val32()
+    D = _dev(A)
+    est = ctx.estimate(D)
+    fl, nz = ctx.symbolic(D)
+    ratio = (nz.double().clamp(min=1) / est.double()).cpu().numpy()
+    assert np.median(np.abs(np.log(ratio))) < 0.05
+    assert np.quantile(ratio, 0.95) < 1.1
+    times = {}
+    outs = {}
+    for name, ue in (("plain", 0), ("learned", 1)):
+        prm = mcl.Params(threshold=1e-4, select_k=1100, recover_pct=0.9, use_estimator=ue)
+        out, ch = ctx.expand(D, prm)  # warm
+        del out
+        torch.cuda.synchronize()
+        t = []
+        for _ in range(3):
+            t0 = time.perf_counter()
+            out, ch = ctx.expand(D, prm)
+            torch.cuda.synchronize()
+            t.append(time.perf_counter() - t0)
+        times[name] = sorted(t)[1]
+        outs[name] = (out, ch)
+    assert times["learned"] < times["plain"], times
+    # same iteration either way
+    assert outs["learned"][0].nnz == outs["plain"][0].nnz
+    assert abs(outs["learned"][1] - outs["plain"][1]) <= 1e-5 * outs["plain"][1]
+    G = outs["learned"][0].to_host()
+    cols = np.random.default_rng(7).choice(A.n, 400, replace=False).astype(np.int32)
+    oprm = oracle.Params(theta=float(np.float32(1e-4)), K=1100, p=float(np.float32(0.9)), r=2.0)
+    rep, _ = compare_iteration(A, G, oprm, cols=cols, rtol=1e-5)
+    assert rep.ok(), rep.failures[:5]
