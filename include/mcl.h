@@ -106,6 +106,7 @@ typedef struct {
     float ms_colstats, ms_estimate, ms_bin, ms_numeric, ms_compact, ms_chaos, ms_total;
     int32_t bins_used;
     int32_t iterations;
+    int32_t phases;           /* column batches of the last mcl_expand */
 } mcl_stats;
 
 /* Create a context on `device` (made current by every call).  alloc/free
@@ -210,6 +211,11 @@ mcl_status mcl_symbolic(mcl_ctx* ctx, const mcl_csc* A, int64_t* flops, int64_t*
  *                        accumulator overflow path (results stay exact)
  *   5 MCL_OPT_ITERATION  iteration index fed to the estimator's features by
  *                        mcl_expand (default 1; mcl_run sets it itself)
+ *   6 MCL_OPT_PHASE_BUDGET  bytes of output staging per column batch; when the
+ *                        staging of all columns, sum_j min(K_rec, flops_j,
+ *                        span_j) pairs of 8 bytes, exceeds it, mcl_expand runs
+ *                        in consecutive column batches that each fit (the
+ *                        phased expansion of Section II, one GPU); 0 = off
  * Returns MCL_ERR_INVALID for an unknown option or value.
  */
 #define MCL_OPT_SIZING 1
@@ -217,6 +223,7 @@ mcl_status mcl_symbolic(mcl_ctx* ctx, const mcl_csc* A, int64_t* flops, int64_t*
 #define MCL_OPT_VALIDATE 3
 #define MCL_OPT_EST_SCALE 4
 #define MCL_OPT_ITERATION 5
+#define MCL_OPT_PHASE_BUDGET 6
 mcl_status mcl_set_option(mcl_ctx* ctx, int option, int64_t value);
 
 /*

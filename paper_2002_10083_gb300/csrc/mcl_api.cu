@@ -33,6 +33,8 @@ struct mcl_ctx {
         cursors, scan, ctr, active, bucket_row, bucket_val, woff, comp_off, comp_of_col,
         comp_bits, comp_active;
     size_t bucket_budget = (size_t)32 << 30;  // bytes of product buckets (large config)
+    size_t phase_budget = 0;                  // bytes of output staging per column batch (0: one)
+    Buf phase_colptr;
     DevCounters* hctr = nullptr;  // pinned host mirror
     mcl_stats stats{};
     cudaEvent_t ev[8] = {};
@@ -267,7 +269,8 @@ void mcl_destroy(mcl_ctx* c) {
     if (!c) return;
     cudaSetDevice(c->device);
     cudaDeviceSynchronize();
-    Buf* all[] = {&c->bucket_row, &c->bucket_val, &c->woff, &c->comp_off, &c->comp_of_col,
+    Buf* all[] = {&c->phase_colptr, &c->bucket_row, &c->bucket_val, &c->woff, &c->comp_off,
+                  &c->comp_of_col,
                   &c->comp_bits, &c->comp_active,
                   &c->flops, &c->rlo,     &c->rhi,     &c->cap,     &c->off,  &c->est,
                   &c->bucket, &c->work,   &c->kept,    &c->chaos,   &c->bnnz, &c->tmp_row,
@@ -306,6 +309,10 @@ mcl_status mcl_set_option(mcl_ctx* c, int option, int64_t value) {
             if (value < 1 || value > 1000000) return fail(c, MCL_ERR_INVALID, "bad scale");
             c->est_milli = (int)value;
             return MCL_OK;
+        case 6:  // column-batch staging budget in bytes (0: one batch)
+            if (value < 0) return fail(c, MCL_ERR_INVALID, "bad budget");
+            c->phase_budget = (size_t)value;
+            return MCL_OK;
         case 5:  // iteration index for the estimator's features
             if (value < 1 || value > 1000000) return fail(c, MCL_ERR_INVALID, "bad iteration");
             c->iteration = (int)value;
@@ -333,23 +340,16 @@ static mcl_status expand_impl(mcl_ctx* c, const mcl_csc* A, const mcl_params* pr
     cudaEventRecord(c->ev[0], s);
     CUDA_TRY(c, cudaMemsetAsync(c->ctr.p, 0, sizeof(DevCounters), s));
     launch_colstats(Av, pp, b, c->num_sms, s);
-    launch_exclusive_scan<int64_t>(b.cap, n, b.off, b.scan_tmp, &b.ctr->cap_total, s);
     if ((st = check_launch(c, "colstats"))) return st;
     cudaEventRecord(c->ev[1], s);
     if ((st = read_counters(c, s))) return st;
     if ((st = err_flags(c, c->hctr->err))) return st;
-    const int64_t cap_total = (int64_t)c->hctr->cap_total;
     const int max_deg = c->hctr->max_deg;
     b.cur_stride = (max_deg + 31) & ~31;
     if (b.cur_stride < 32) b.cur_stride = 32;
     const int grid_max = max_numeric_grid(c, pp.ksel);
-    if (!ensure(c, c->tmp_row, (size_t)cap_total * 4 + 4, s) ||
-        !ensure(c, c->tmp_val, (size_t)cap_total * 4 + 4, s) ||
-        !ensure(c, c->cursors, (size_t)grid_max * 6 * b.cur_stride * 4, s))
-        return fail(c, MCL_ERR_OOM, "scratch allocation failed (capacity %lld)",
-                    (long long)cap_total);
-    b.tmp_row = (int32_t*)c->tmp_row.p;
-    b.tmp_val = (float*)c->tmp_val.p;
+    if (!ensure(c, c->cursors, (size_t)grid_max * 6 * b.cur_stride * 4, s))
+        return fail(c, MCL_ERR_OOM, "cursor scratch allocation failed");
     b.cursors = (int32_t*)c->cursors.p;
     // ---- size estimate ----
     const int sizing = c->sizing >= 0 ? c->sizing : (prm->use_estimator ? 2 : 0);
@@ -361,68 +361,193 @@ static mcl_status expand_impl(mcl_ctx* c, const mcl_csc* A, const mcl_params* pr
         launch_est_from_flops(Av, b, s);
     } else {
         launch_symbolic(Av, b, b.est, c->num_sms, grid_max, s);
+        // exact counts bound each column's output: cap_j = min(cap_j, nnz_j)
+        launch_cap_tighten((int32_t)n, b.est, b.cap, active, s);
     }
     if (c->est_milli != 1000) launch_scale_est(A->n, b.est, c->est_milli, s);
     if ((st = check_launch(c, "estimate"))) return st;
+    launch_exclusive_scan<int64_t>(b.cap, n, b.off, b.scan_tmp, &b.ctr->cap_total, s);
     cudaEventRecord(c->ev[2], s);
-    // ---- binning + numeric ----
-    launch_binning(Av, pp, b, c->conf_mask, s);
-    cudaEventRecord(c->ev[3], s);
+    if ((st = read_counters(c, s))) return st;
+    const int64_t cap_total = (int64_t)c->hctr->cap_total;
+    // column batches (phases): the output staging of a batch fits the budget
+    int64_t budget_entries = c->phase_budget > 0 ? (int64_t)(c->phase_budget / 8) : 0;
+    if (budget_entries > 0 && budget_entries < pp.Krec) budget_entries = pp.Krec;
+    const bool phased = budget_entries > 0 && cap_total > budget_entries && active == nullptr;
+    const int64_t stage = phased ? budget_entries : cap_total;
+    if (!ensure(c, c->tmp_row, (size_t)stage * 4 + 4, s) ||
+        !ensure(c, c->tmp_val, (size_t)stage * 4 + 4, s))
+        return fail(c, MCL_ERR_OOM, "scratch allocation failed (capacity %lld)", (long long)stage);
+    b.tmp_row = (int32_t*)c->tmp_row.p;
+    b.tmp_val = (float*)c->tmp_val.p;
+    b.tmp_off0 = 0;
+    // ---- binning + numeric over the columns a mask selects ----
     int used = 0;
-    for (int q = NCONF - 1; q >= 0; --q) {
-        if (!((c->conf_mask >> q) & 1)) continue;
-        int g = numeric_grid(q, pp.ksel, c->num_sms);
-        ExpandBuffers bq = b;
-        bq.bucket_row = nullptr;
-        bq.bucket_val = nullptr;
-        bq.woff = nullptr;
-        bq.bucket_cap = 0;
-        if (q == NCONF - 1) {
-            // product buckets for multi-window columns of the large configuration
-            const int64_t maxf = (int64_t)c->hctr->max_flops;
-            int64_t capb = (int64_t)(c->bucket_budget / ((size_t)g * 8));
-            if (capb > maxf) capb = maxf;
-            if (capb >= 1024 &&
-                ensure(c, c->bucket_row, (size_t)g * capb * 4, s) &&
-                ensure(c, c->bucket_val, (size_t)g * capb * 4, s) &&
-                ensure(c, c->woff, (size_t)g * (WINDOW_MAX + 1) * 4, s)) {
-                bq.bucket_row = (int32_t*)c->bucket_row.p;
-                bq.bucket_val = (float*)c->bucket_val.p;
-                bq.woff = (int32_t*)c->woff.p;
-                bq.bucket_cap = capb;
+    auto run_numeric = [&](const ExpandBuffers& bb) -> mcl_status {
+        launch_binning(Av, pp, bb, c->conf_mask, s);
+        for (int q = NCONF - 1; q >= 0; --q) {
+            if (!((c->conf_mask >> q) & 1)) continue;
+            const int g = numeric_grid(q, pp.ksel, c->num_sms);
+            ExpandBuffers bq = bb;
+            bq.bucket_row = nullptr;
+            bq.bucket_val = nullptr;
+            bq.woff = nullptr;
+            bq.bucket_cap = 0;
+            if (q == NCONF - 1) {
+                // product buckets for multi-window columns of the large configuration
+                const int64_t maxf = (int64_t)c->hctr->max_flops;
+                int64_t capb = (int64_t)(c->bucket_budget / ((size_t)g * 8));
+                if (capb > maxf) capb = maxf;
+                if (capb >= 1024 && ensure(c, c->bucket_row, (size_t)g * capb * 4, s) &&
+                    ensure(c, c->bucket_val, (size_t)g * capb * 4, s) &&
+                    ensure(c, c->woff, (size_t)g * (WINDOW_MAX + 1) * 4, s)) {
+                    bq.bucket_row = (int32_t*)c->bucket_row.p;
+                    bq.bucket_val = (float*)c->bucket_val.p;
+                    bq.woff = (int32_t*)c->woff.p;
+                    bq.bucket_cap = capb;
+                }
+            }
+            launch_numeric(q, Av, pp, bq, g, s);
+            ++used;
+        }
+        return check_launch(c, "numeric");
+    };
+    int64_t* colptr_out = nullptr;
+    int32_t* row_out = nullptr;
+    float* val_out = nullptr;
+    int64_t nnz_out = 0;
+    int phases = 1;
+    if (!phased) {
+        cudaEventRecord(c->ev[3], s);
+        if ((st = run_numeric(b))) return st;
+        cudaEventRecord(c->ev[4], s);
+        launch_finalize_stats(A->n, b, s);
+        // ---- output ----
+        colptr_out = (int64_t*)dev_alloc(c, (size_t)(n + 1) * 8, s);
+        if (!colptr_out) return fail(c, MCL_ERR_OOM, "output colptr allocation failed");
+        if (active) launch_fill_inactive(Av, active, b.kept, s);  // carried columns keep their length
+        launch_exclusive_scan<int32_t>(b.kept, n, colptr_out, b.scan_tmp, &b.ctr->nnz_out, s);
+        if ((st = check_launch(c, "scan"))) {
+            dev_free(c, colptr_out, s);
+            return st;
+        }
+        cudaEventRecord(c->ev[5], s);
+        if ((st = read_counters(c, s)) || (st = err_flags(c, c->hctr->err))) {
+            dev_free(c, colptr_out, s);
+            return st;
+        }
+        nnz_out = (int64_t)c->hctr->nnz_out;
+        row_out = (int32_t*)dev_alloc(c, (size_t)nnz_out * 4 + 4, s);
+        val_out = (float*)dev_alloc(c, (size_t)nnz_out * 4 + 4, s);
+        if (!row_out || !val_out) {
+            dev_free(c, colptr_out, s);
+            dev_free(c, row_out, s);
+            dev_free(c, val_out, s);
+            return fail(c, MCL_ERR_OOM, "output allocation failed (nnz %lld)", (long long)nnz_out);
+        }
+        launch_compact(Av, b, colptr_out, row_out, val_out, s);
+        if ((st = check_launch(c, "compact"))) return st;
+    } else {
+        // plan consecutive column batches whose capacities fit the staging budget
+        std::vector<int64_t> hoff((size_t)n + 1);
+        CUDA_TRY(c, cudaMemcpyAsync(hoff.data(), b.off, ((size_t)n + 1) * 8, cudaMemcpyDeviceToHost, s));
+        CUDA_TRY(c, cudaStreamSynchronize(s));
+        std::vector<int32_t> cut;
+        cut.push_back(0);
+        while (cut.back() < n) {
+            const int32_t c0 = cut.back();
+            int64_t lo = c0 + 1, hi = n;  // largest c1 with hoff[c1] - hoff[c0] <= budget
+            while (lo < hi) {
+                const int64_t mid = (lo + hi + 1) / 2;
+                if (hoff[mid] - hoff[c0] <= budget_entries) lo = mid; else hi = mid - 1;
+            }
+            cut.push_back((int32_t)lo);
+        }
+        phases = (int)cut.size() - 1;
+        if (!ensure(c, c->active, (size_t)n + 1, s) ||
+            !ensure(c, c->phase_colptr, ((size_t)n + 2) * 8, s))
+            return fail(c, MCL_ERR_OOM, "batch scratch allocation failed");
+        uint8_t* mask = (uint8_t*)c->active.p;
+        int64_t* pcol = (int64_t*)c->phase_colptr.p;
+        std::vector<int32_t*> seg_row;
+        std::vector<float*> seg_val;
+        std::vector<int64_t> seg_nnz;
+        auto free_segments = [&]() {
+            for (size_t q = 0; q < seg_row.size(); ++q) {
+                dev_free(c, seg_row[q], s);
+                dev_free(c, seg_val[q], s);
+            }
+        };
+        cudaEventRecord(c->ev[3], s);
+        for (int ph = 0; ph < phases; ++ph) {
+            const int32_t c0 = cut[ph], c1 = cut[ph + 1];
+            launch_range_mask((int32_t)n, c0, c1, mask, s);
+            ExpandBuffers bb = b;
+            bb.active = mask;
+            bb.tmp_off0 = hoff[c0];
+            if ((st = run_numeric(bb))) {
+                free_segments();
+                return st;
+            }
+            launch_exclusive_scan<int32_t>(b.kept + c0, c1 - c0, pcol, b.scan_tmp, &b.ctr->nnz_out, s);
+            if ((st = read_counters(c, s)) || (st = err_flags(c, c->hctr->err))) {
+                free_segments();
+                return st;
+            }
+            const int64_t nb = (int64_t)c->hctr->nnz_out;
+            int32_t* r = (int32_t*)dev_alloc(c, (size_t)nb * 4 + 4, s);
+            float* v = (float*)dev_alloc(c, (size_t)nb * 4 + 4, s);
+            seg_row.push_back(r);
+            seg_val.push_back(v);
+            seg_nnz.push_back(nb);
+            if (!r || !v) {
+                free_segments();
+                return fail(c, MCL_ERR_OOM, "batch output allocation failed");
+            }
+            launch_compact_range(Av, bb, c0, c1, pcol, r, v, s);
+            if ((st = check_launch(c, "batch compact"))) {
+                free_segments();
+                return st;
             }
         }
-        launch_numeric(q, Av, pp, bq, g, s);
-        ++used;
+        cudaEventRecord(c->ev[4], s);
+        launch_finalize_stats(A->n, b, s);
+        colptr_out = (int64_t*)dev_alloc(c, (size_t)(n + 1) * 8, s);
+        if (!colptr_out) {
+            free_segments();
+            return fail(c, MCL_ERR_OOM, "output colptr allocation failed");
+        }
+        launch_exclusive_scan<int32_t>(b.kept, n, colptr_out, b.scan_tmp, &b.ctr->nnz_out, s);
+        cudaEventRecord(c->ev[5], s);
+        if ((st = read_counters(c, s)) || (st = err_flags(c, c->hctr->err))) {
+            free_segments();
+            dev_free(c, colptr_out, s);
+            return st;
+        }
+        nnz_out = (int64_t)c->hctr->nnz_out;
+        row_out = (int32_t*)dev_alloc(c, (size_t)nnz_out * 4 + 4, s);
+        val_out = (float*)dev_alloc(c, (size_t)nnz_out * 4 + 4, s);
+        if (!row_out || !val_out) {
+            free_segments();
+            dev_free(c, colptr_out, s);
+            dev_free(c, row_out, s);
+            dev_free(c, val_out, s);
+            return fail(c, MCL_ERR_OOM, "output allocation failed (nnz %lld)", (long long)nnz_out);
+        }
+        // the batches are consecutive column ranges: their segments concatenate
+        int64_t at = 0;
+        for (size_t q = 0; q < seg_row.size(); ++q) {
+            if (seg_nnz[q] > 0) {
+                CUDA_TRY(c, cudaMemcpyAsync(row_out + at, seg_row[q], (size_t)seg_nnz[q] * 4,
+                                            cudaMemcpyDeviceToDevice, s));
+                CUDA_TRY(c, cudaMemcpyAsync(val_out + at, seg_val[q], (size_t)seg_nnz[q] * 4,
+                                            cudaMemcpyDeviceToDevice, s));
+            }
+            at += seg_nnz[q];
+        }
+        free_segments();
+        if (at != nnz_out) return fail(c, MCL_ERR_INTERNAL, "batch outputs do not add up");
     }
-    if ((st = check_launch(c, "numeric"))) return st;
-    cudaEventRecord(c->ev[4], s);
-    launch_finalize_stats(A->n, b, s);
-    // ---- output ----
-    int64_t* colptr_out = (int64_t*)dev_alloc(c, (size_t)(n + 1) * 8, s);
-    if (!colptr_out) return fail(c, MCL_ERR_OOM, "output colptr allocation failed");
-    if (active) launch_fill_inactive(Av, active, b.kept, s);  // carried columns keep their length
-    launch_exclusive_scan<int32_t>(b.kept, n, colptr_out, b.scan_tmp, &b.ctr->nnz_out, s);
-    if ((st = check_launch(c, "scan"))) {
-        dev_free(c, colptr_out, s);
-        return st;
-    }
-    cudaEventRecord(c->ev[5], s);
-    if ((st = read_counters(c, s)) || (st = err_flags(c, c->hctr->err))) {
-        dev_free(c, colptr_out, s);
-        return st;
-    }
-    const int64_t nnz_out = (int64_t)c->hctr->nnz_out;
-    int32_t* row_out = (int32_t*)dev_alloc(c, (size_t)nnz_out * 4 + 4, s);
-    float* val_out = (float*)dev_alloc(c, (size_t)nnz_out * 4 + 4, s);
-    if (!row_out || !val_out) {
-        dev_free(c, colptr_out, s);
-        dev_free(c, row_out, s);
-        dev_free(c, val_out, s);
-        return fail(c, MCL_ERR_OOM, "output allocation failed (nnz %lld)", (long long)nnz_out);
-    }
-    launch_compact(Av, b, colptr_out, row_out, val_out, s);
-    if ((st = check_launch(c, "compact"))) return st;
     cudaEventRecord(c->ev[6], s);
     out->n = A->n;
     out->nnz = nnz_out;
@@ -441,6 +566,7 @@ static mcl_status expand_impl(mcl_ctx* c, const mcl_csc* A, const mcl_params* pr
     S.range_splits = (int64_t)c->hctr->splits;
     S.chaos = ch;
     S.bins_used = used;
+    S.phases = phases;
     cudaEventElapsedTime(&S.ms_colstats, c->ev[0], c->ev[1]);
     cudaEventElapsedTime(&S.ms_estimate, c->ev[1], c->ev[2]);
     cudaEventElapsedTime(&S.ms_bin, c->ev[2], c->ev[3]);

@@ -73,8 +73,9 @@ struct ExpandBuffers {
     int32_t* kept;      // [n]
     double* chaos;      // [n]
     int64_t* bnnz;      // [n]
-    int32_t* tmp_row;   // [cap_total]
+    int32_t* tmp_row;   // [cap_total] (or one column batch's share)
     float* tmp_val;     // [cap_total]
+    int64_t tmp_off0;   // staging index of column j is off[j] - tmp_off0
     int32_t* cursors;   // per CTA: source metadata, 6 * cur_stride int32
     int64_t cur_stride;
     int32_t* bucket_row;   // per CTA: bucket_cap products (row) of the current column
@@ -102,6 +103,8 @@ void launch_symbolic(const CscView& A, const ExpandBuffers& b, int64_t* nnz_out,
                      int grid_cap, cudaStream_t s);
 int symbolic_grid(int num_sms);
 void launch_scale_est(int32_t n, int64_t* est, int milli, cudaStream_t s);
+void launch_cap_tighten(int32_t n, const int64_t* est, int64_t* cap, const uint8_t* active,
+                        cudaStream_t s);
 void launch_est_from_flops(const CscView& A, const ExpandBuffers& b, cudaStream_t s);
 void launch_binning(const CscView& A, const PruneParams& pp, const ExpandBuffers& b, int mask,
                     cudaStream_t s);
@@ -115,6 +118,10 @@ void launch_numeric(int conf, const CscView& A, const PruneParams& pp, const Exp
 void launch_compact(const CscView& A, const ExpandBuffers& b, const int64_t* colptr_out,
                     int32_t* row_out, float* val_out, cudaStream_t s);
 void launch_finalize_stats(int32_t n, const ExpandBuffers& b, cudaStream_t s);
+void launch_range_mask(int32_t n, int32_t c0, int32_t c1, uint8_t* mask, cudaStream_t s);
+void launch_compact_range(const CscView& A, const ExpandBuffers& b, int32_t c0, int32_t c1,
+                          const int64_t* colptr_local, int32_t* row_out, float* val_out,
+                          cudaStream_t s);
 void launch_prune_cap(const CscView& B, int32_t Krec, const ExpandBuffers& b, cudaStream_t s);
 void launch_prune(const CscView& B, const PruneParams& pp, const ExpandBuffers& b, int num_sms,
                   cudaStream_t s);

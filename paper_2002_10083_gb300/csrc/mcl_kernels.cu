@@ -394,6 +394,20 @@ void launch_scale_est(int32_t n, int64_t* est, int milli, cudaStream_t s) {
     count_launches(1);
 }
 
+// cap_j = min(cap_j, nnz_j) for active columns when nnz_j is exact
+__global__ void k_cap_tighten(int32_t n, const int64_t* est, int64_t* cap, const uint8_t* active) {
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n || (active && !active[j])) return;
+    if (est[j] < cap[j]) cap[j] = est[j];
+}
+
+void launch_cap_tighten(int32_t n, const int64_t* est, int64_t* cap, const uint8_t* active,
+                        cudaStream_t s) {
+    if (n == 0) return;
+    k_cap_tighten<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, est, cap, active);
+    count_launches(1);
+}
+
 void launch_est_from_flops(const CscView& A, const ExpandBuffers& b, cudaStream_t s) {
     if (A.n == 0) return;
     k_est_from_flops<<<(unsigned)((A.n + 255) / 256), 256, 0, s>>>(A.n, b);
@@ -518,13 +532,53 @@ __global__ void k_compact(CscView A, ExpandBuffers b, const int64_t* colptr_out,
                 val_out[dst + i] = A.val[src + i];
             }
         } else {
-            const int64_t src = b.off[j];
+            const int64_t src = b.off[j] - b.tmp_off0;
             for (int64_t i = lane; i < len; i += 32) {
                 row_out[dst + i] = b.tmp_row[src + i];
                 val_out[dst + i] = b.tmp_val[src + i];
             }
         }
     }
+}
+
+// Compaction of one column batch [c0, c1): colptr_local[j - c0] indexes
+// the batch's own output segment.
+__global__ void k_compact_range(ExpandBuffers b, int32_t c0, int32_t c1,
+                                const int64_t* colptr_local, int32_t* row_out, float* val_out) {
+    const int lane = threadIdx.x & 31;
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t j = c0 + gw; j < c1; j += nw) {
+        const int64_t dst = colptr_local[j - c0];
+        const int64_t len = colptr_local[j - c0 + 1] - dst;
+        const int64_t src = b.off[j] - b.tmp_off0;
+        for (int64_t i = lane; i < len; i += 32) {
+            row_out[dst + i] = b.tmp_row[src + i];
+            val_out[dst + i] = b.tmp_val[src + i];
+        }
+    }
+}
+
+void launch_compact_range(const CscView& A, const ExpandBuffers& b, int32_t c0, int32_t c1,
+                          const int64_t* colptr_local, int32_t* row_out, float* val_out,
+                          cudaStream_t s) {
+    (void)A;
+    if (c1 <= c0) return;
+    int64_t blocks = ((int64_t)(c1 - c0) * 32 + 255) / 256;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    k_compact_range<<<(unsigned)blocks, 256, 0, s>>>(b, c0, c1, colptr_local, row_out, val_out);
+    count_launches(1);
+}
+
+__global__ void k_range_mask(int32_t n, int32_t c0, int32_t c1, uint8_t* mask) {
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < n) mask[j] = (j >= c0 && j < c1) ? 1 : 0;
+}
+
+void launch_range_mask(int32_t n, int32_t c0, int32_t c1, uint8_t* mask, cudaStream_t s) {
+    if (n == 0) return;
+    k_range_mask<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, c0, c1, mask);
+    count_launches(1);
 }
 
 void launch_compact(const CscView& A, const ExpandBuffers& b, const int64_t* colptr_out,

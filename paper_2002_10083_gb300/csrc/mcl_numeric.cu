@@ -820,8 +820,9 @@ __global__ void __launch_bounds__(T, MINB) k_expand(ExpandArgs a) {
         int mstar = 0;
         double ch = 0.0;
         const int64_t obase = b.off[j];
-        finish_column<T, IPT>(top, ntop, a.pp, dv[0], dv[1], qv[0], b.cap[j], b.tmp_row + obase,
-                              b.tmp_val + obase, hist, mhist, sh, ctr, &mstar, &ch);
+        finish_column<T, IPT>(top, ntop, a.pp, dv[0], dv[1], qv[0], b.cap[j],
+                              b.tmp_row + (obase - b.tmp_off0), b.tmp_val + (obase - b.tmp_off0),
+                              hist, mhist, sh, ctr, &mstar, &ch);
         if (tid == 0) {
             b.kept[j] = mstar;
             b.chaos[j] = ch;
@@ -946,8 +947,9 @@ __global__ void __launch_bounds__(PR_T) k_prune(PruneArgs2 a) {
         int mstar = 0;
         double ch = 0.0;
         const int64_t obase = b.off[j];
-        finish_column<PR_T, 8>(top, ntop, a.pp, dv[0], dv[1], qv[0], b.cap[j], b.tmp_row + obase,
-                               b.tmp_val + obase, hist, mhist, sh, b.ctr, &mstar, &ch);
+        finish_column<PR_T, 8>(top, ntop, a.pp, dv[0], dv[1], qv[0], b.cap[j],
+                               b.tmp_row + (obase - b.tmp_off0), b.tmp_val + (obase - b.tmp_off0),
+                               hist, mhist, sh, b.ctr, &mstar, &ch);
         if (tid == 0) {
             b.kept[j] = mstar;
             b.chaos[j] = ch;

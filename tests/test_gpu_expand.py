@@ -335,3 +335,28 @@ def test_batched_rejects_non_block_diagonal(ctx):
     with pytest.raises(mcl.MclError) as ei:
         ctx.run(_dev(A), prm, comp_offsets=np.array([0, 50, 100], np.int32))
     assert ei.value.status == 1
+
+
+@pytest.mark.parametrize("budget", [64 * 1024, 1 << 20])
+def test_column_batched_expansion_equals_single_pass(ctx, budget):
+    """Consecutive column batches whose output staging fits a budget (the
+    phased expansion) give the same iteration as one pass."""
+    from paper_2002_10083_gb300 import mcl
+    A = synth.chung_lu(n=30000, mean=30.0, d_max=2000, seed=8).with_val32()
+    D = _dev(A)
+    prm = _prm(K=500, p=0.9)
+    ref, ch_ref = ctx.expand(D, prm)
+    try:
+        ctx.set_option(mcl.OPT_PHASE_BUDGET, budget)
+        out, ch = ctx.expand(D, prm)
+        phases = ctx.stats()["phases"]
+    finally:
+        ctx.set_option(mcl.OPT_PHASE_BUDGET, 0)
+    assert phases > 1
+    assert torch.equal(out.colptr, ref.colptr) and torch.equal(out.rowidx, ref.rowidx)
+    assert torch.allclose(out.val, ref.val, rtol=RTOL, atol=0)
+    # FP32 atomic accumulation order differs between runs (values agree to 1e-5)
+    assert abs(ch - ch_ref) <= 3 * RTOL * ch_ref
+    cols = np.random.default_rng(5).choice(A.n, 500, replace=False).astype(np.int32)
+    rep, _ = compare_iteration(A, out.to_host(), _oprm(prm), cols=cols, rtol=RTOL)
+    assert rep.ok(), rep.failures[:5]
