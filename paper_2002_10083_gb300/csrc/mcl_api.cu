@@ -29,7 +29,7 @@ struct mcl_ctx {
     void* user = nullptr;
     char err[512] = {0};
     // scratch
-    Buf flops, rlo, rhi, cap, off, est, bucket, work, kept, chaos, bnnz, tmp_row, tmp_val,
+    Buf flops, colsum, rlo, rhi, cap, off, est, bucket, work, kept, chaos, bnnz, tmp_row, tmp_val,
         cursors, scan, ctr, active, bucket_row, bucket_val, woff, comp_off, comp_of_col,
         comp_bits, comp_active;
     size_t bucket_budget = (size_t)32 << 30;  // bytes of product buckets (large config)
@@ -155,6 +155,7 @@ CscView view(const mcl_csc* A) {
 ExpandBuffers buffers(mcl_ctx* c) {
     ExpandBuffers b{};
     b.flops = (int64_t*)c->flops.p;
+    b.colsum = (double*)c->colsum.p;
     b.rlo = (int32_t*)c->rlo.p;
     b.rhi = (int32_t*)c->rhi.p;
     b.cap = (int64_t*)c->cap.p;
@@ -181,7 +182,8 @@ ExpandBuffers buffers(mcl_ctx* c) {
 
 mcl_status ensure_columns(mcl_ctx* c, int64_t n, cudaStream_t s) {
     const size_t n1 = (size_t)n + 1;
-    bool ok = ensure(c, c->flops, n1 * 8, s) && ensure(c, c->rlo, n1 * 4, s) &&
+    bool ok = ensure(c, c->flops, n1 * 8, s) && ensure(c, c->colsum, n1 * 8, s) &&
+              ensure(c, c->rlo, n1 * 4, s) &&
               ensure(c, c->rhi, n1 * 4, s) && ensure(c, c->cap, n1 * 8, s) &&
               ensure(c, c->off, n1 * 8, s) && ensure(c, c->est, n1 * 8, s) &&
               ensure(c, c->bucket, n1 * 4, s) && ensure(c, c->work, n1 * 4, s) &&
@@ -272,7 +274,7 @@ void mcl_destroy(mcl_ctx* c) {
     Buf* all[] = {&c->phase_colptr, &c->bucket_row, &c->bucket_val, &c->woff, &c->comp_off,
                   &c->comp_of_col,
                   &c->comp_bits, &c->comp_active,
-                  &c->flops, &c->rlo,     &c->rhi,     &c->cap,     &c->off,  &c->est,
+                  &c->flops, &c->colsum, &c->rlo, &c->rhi,  &c->cap,     &c->off,  &c->est,
                   &c->bucket, &c->work,   &c->kept,    &c->chaos,   &c->bnnz, &c->tmp_row,
                   &c->tmp_val, &c->cursors, &c->scan,  &c->ctr,     &c->active, &c->mlp_w,
                   &c->mlp_norm, &c->colmax, &c->feats, &c->prev_logcf};

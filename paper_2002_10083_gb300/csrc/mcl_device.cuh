@@ -212,8 +212,8 @@ __device__ int block_select_mass(const uint64_t* A, int na, double target, uint6
     const float maxv = key_val((uint64_t)bs->q[3][32]);
     int e = 0;
     frexpf(maxv > 0.0f ? maxv : 1.0f, &e);  // maxv < 2^e
-    const double scale = ldexp(1.0, 50 - e);
-    const double tf = ceil(target * scale);
+    const int sh50 = 50 - e;                // v * 2^sh50 < 2^50 is exact in FP32
+    const double tf = ceil(ldexp(target, sh50));
     if (!(tf < 9.0e18)) {  // beyond any reachable sum
         __syncthreads();
         return 0;
@@ -240,7 +240,7 @@ __device__ int block_select_mass(const uint64_t* A, int na, double target, uint6
                 const unsigned grp = __match_any_sync(act, dg);
                 // group sum of the fixed-point masses (< 2^50 each) as two
                 // 25-bit halves, each summed exactly in 32 bits
-                const unsigned long long fx = (unsigned long long)((double)key_val(x) * scale);
+                const unsigned long long fx = __float2ull_rz(ldexpf(key_val(x), sh50));
                 const unsigned lo25 = __reduce_add_sync(grp, (unsigned)(fx & 0x1FFFFFFull));
                 const unsigned hi25 = __reduce_add_sync(grp, (unsigned)(fx >> 25));
                 if (__ffs(grp) - 1 == lane) {

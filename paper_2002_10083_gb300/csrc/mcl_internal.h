@@ -63,6 +63,7 @@ struct PruneParams {
 
 struct ExpandBuffers {
     int64_t* flops;     // [n]
+    double* colsum;     // [n]   column sums of A (FP64)
     int32_t* rlo;       // [n]
     int32_t* rhi;       // [n]
     int64_t* cap;       // [n]   output capacity min(Krec, flops, span)

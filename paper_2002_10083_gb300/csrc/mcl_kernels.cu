@@ -65,9 +65,11 @@ __global__ void k_colstats(CscView A, int32_t Krec, ExpandBuffers b) {
         long long f = 0;
         int mn = INT_MAX, mx = -1;
         unsigned bad = 0;
+        double csum = 0.0;
         for (int64_t p = cb + lane; p < ce; p += 32) {
             const int k = A.rowidx[p];
             const float v = A.val[p];
+            csum += (double)v;
             if (!(v >= 0.0f) || !(v <= FLT_MAX)) bad |= ERR_VALUE;
             if (p > cb && A.rowidx[p - 1] >= k) bad |= ERR_ROW_ORDER;
             if ((unsigned)k >= (unsigned)A.n) {
@@ -88,6 +90,7 @@ __global__ void k_colstats(CscView A, int32_t Krec, ExpandBuffers b) {
         }
         bad = __reduce_or_sync(FULL, bad);
         f = warp_sum(f);
+        csum = warp_sum(csum);
         mn = warp_min(mn);
         mx = warp_max(mx);
         if (lane == 0) {
@@ -95,6 +98,7 @@ __global__ void k_colstats(CscView A, int32_t Krec, ExpandBuffers b) {
             const bool any = f > 0 && mx >= mn && mn >= 0;
             const int span = any ? (mx - mn + 1) : 0;
             b.flops[j] = f;
+            if (b.colsum) b.colsum[j] = csum;
             b.rlo[j] = any ? mn : 0;
             b.rhi[j] = any ? mx : -1;
             long long cap = f < (long long)span ? f : (long long)span;

@@ -206,6 +206,7 @@ __device__ void finish_column(uint64_t* top, int ntop, const PruneParams& pp, do
     long long qv[1] = {0};
     block_sum<T>(dv, 1, qv, 0, &sh->bs);
     const double U = dv[0];
+    const double invU = U > 0.0 ? 1.0 / U : 0.0;
     int tot;
     int o = block_scan_excl<T>(c, &tot, sh->wsm);
     if (tid == 0 && tot != mstar) set_err2(ctr, ERR_INTERNAL);
@@ -218,7 +219,7 @@ __device__ void finish_column(uint64_t* top, int ntop, const PruneParams& pp, do
                 const float v = key_val(x);
                 float outv = v;
                 if (pp.inflate) {
-                    const double a = U > 0.0 ? (double)inflate_value(v, pp.r) / U : 0.0;
+                    const double a = (double)inflate_value(v, pp.r) * invU;
                     outv = (float)a;
                     amax = a > amax ? a : amax;
                     asq += a * a;
@@ -431,13 +432,18 @@ __global__ void __launch_bounds__(T, MINB) k_expand(ExpandArgs a) {
         const int64_t flops_j = b.flops[j];
         int64_t est = b.est[j];
         if (est < 1) est = 1;
+        // column sum of B_*j from the identity sum_i (AA)_ij = sum_k a_kj sum_i a_ik
+        // (FP64; exact up to FP64 rounding, independent of the FP32 accumulation)
+        double s_sum = 0.0;
         for (int i = tid; i < d; i += T) {
             const int k = A.rowidx[cb + i];
             const int64_t ks = A.colptr[k];
+            const float akj = A.val[cb + i];
             meta.ks[i] = ks;
             meta.len[i] = (int)(A.colptr[k + 1] - ks);
             meta.cur[i] = 0;
-            meta.akj[i] = A.val[cb + i];
+            meta.akj[i] = akj;
+            s_sum += (double)akj * b.colsum[k];
         }
         // ---- plan: one window, bucketed windows, or source-cursor windows ----
         int nwin = 1, width = span;
@@ -455,7 +461,7 @@ __global__ void __launch_bounds__(T, MINB) k_expand(ExpandArgs a) {
         }
         int ntop = 0;
         uint64_t tau = 0;
-        double s_sum = 0.0, s_mt = 0.0;
+        double s_mt = 0.0;
         long long s_t = 0, s_n = 0;
         FastDiv fdiv;
         fdiv.init((uint32_t)width);
@@ -787,13 +793,12 @@ __global__ void __launch_bounds__(T, MINB) k_expand(ExpandArgs a) {
                 if (w >= nwc) break;
                 uint32_t m = bm[w];
                 int r = pre[w];
+                s_n += __popc(m);
                 while (m) {
                     const int bb = __ffs(m) - 1;
                     m &= m - 1;
                     const float v = vals[r];
                     ++r;
-                    s_sum += (double)v;
-                    ++s_n;
                     if (v >= a.pp.theta) {
                         ++s_t;
                         s_mt += (double)v;
