@@ -242,6 +242,12 @@ def run_gpu(args):
     # the other form, same workload, for the comparison the metric asks for
     other = prm_plain if prm_main is prm_learn else prm_learn
     ms_o, t_num_o, st_o = _time_form(ctx, D, other, args.steps, stream, torch, mcl)
+    # Cohen's probabilistic estimate (Section V) as the size estimate
+    ctx.set_option(mcl.OPT_SIZING, mcl.SIZING_COHEN)
+    out, ch = ctx.expand(D, prm_plain)
+    del out
+    ms_c, t_num_c, st_c = _time_form(ctx, D, prm_plain, args.steps, stream, torch, mcl)
+    ctx.set_option(mcl.OPT_SIZING, mcl.SIZING_PARAMS)
 
     # end to end through the C ABI with host buffers (pinned): H2D of A,
     # the iteration, D2H of the resulting matrix
@@ -306,6 +312,7 @@ def run_gpu(args):
         "iters_per_s": round(world * 1000.0 / ms, 3),
         main_name: form_line(ms, t_num, st),
         other_name: form_line(ms_o, t_num_o, st_o),
+        "cohen": form_line(ms_c, t_num_c, st_c),
         "speedup_learned_vs_plain": round((ms_o / ms) if main_name == "learned" else (ms / ms_o), 4),
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 4), "traffic": None,

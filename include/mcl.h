@@ -202,7 +202,8 @@ mcl_status mcl_symbolic(mcl_ctx* ctx, const mcl_csc* A, int64_t* flops, int64_t*
 /*
  * Tuning options of a context (not part of the method):
  *   1 MCL_OPT_SIZING     -1 follow prm->use_estimator (default), 0 exact
- *                        symbolic pass, 1 the flops bound min(flops_j, span_j)
+ *                        symbolic pass, 1 the flops bound min(flops_j, span_j),
+ *                        3 Cohen's estimate (mcl_cohen_estimate)
  *   2 MCL_OPT_CONF_MASK  bit mask of numeric-pass configurations (bit 0:
  *                        small CTA and window, bit 1: large; not 0)
  *   3 MCL_OPT_VALIDATE   1 (default) validate inputs
@@ -216,6 +217,8 @@ mcl_status mcl_symbolic(mcl_ctx* ctx, const mcl_csc* A, int64_t* flops, int64_t*
  *                        span_j) pairs of 8 bytes, exceeds it, mcl_expand runs
  *                        in consecutive column batches that each fit (the
  *                        phased expansion of Section II, one GPU); 0 = off
+ *   7 MCL_OPT_COHEN_KEYS keys per vertex of Cohen's estimate (2..16, default 8)
+ *   8 MCL_OPT_COHEN_SEED seed of Cohen's keys (default 2002)
  * Returns MCL_ERR_INVALID for an unknown option or value.
  */
 #define MCL_OPT_SIZING 1
@@ -224,6 +227,8 @@ mcl_status mcl_symbolic(mcl_ctx* ctx, const mcl_csc* A, int64_t* flops, int64_t*
 #define MCL_OPT_EST_SCALE 4
 #define MCL_OPT_ITERATION 5
 #define MCL_OPT_PHASE_BUDGET 6
+#define MCL_OPT_COHEN_KEYS 7
+#define MCL_OPT_COHEN_SEED 8
 mcl_status mcl_set_option(mcl_ctx* ctx, int option, int64_t value);
 
 /*
@@ -279,6 +284,20 @@ mcl_status mcl_adam_step(mcl_ctx* ctx, float* master, float* m, float* v, const 
 /* The size estimate the numeric pass would use with the loaded estimator
  * (iteration from MCL_OPT_ITERATION), into est (int64[n]). */
 mcl_status mcl_estimate(mcl_ctx* ctx, const mcl_csc* A, int64_t* est, void* stream);
+
+/*
+ * Cohen's probabilistic output-size estimate (Section V): each row i of A
+ * gets `keys` (r, 2..16) FP32 keys -ln(u) with u from splitmix64 at counter
+ * seed + (i*r + l) * 0x9E3779B97F4A7C15 (top 53 bits + 1, over 2^53); the
+ * minimum key l over each column's rows, then over each column's sources,
+ * gives est_j = (r - 1) / sum_l min_l (0 for an empty column), the
+ * estimate of nnz((AA)_*j), in O(r nnz(A)).  est: device float[n].
+ * MCL_OPT_SIZING = 3 makes mcl_expand size its windows with it
+ * (MCL_OPT_COHEN_KEYS, MCL_OPT_COHEN_SEED).  A is validated first (one
+ * synchronisation; MCL_ERR_INVALID for a malformed A or keys outside 2..16).
+ */
+mcl_status mcl_cohen_estimate(mcl_ctx* ctx, const mcl_csc* A, int32_t keys, uint64_t seed,
+                              float* est, void* stream);
 
 /* Statistics of the last mcl_expand / mcl_run on ctx. */
 mcl_status mcl_get_stats(mcl_ctx* ctx, mcl_stats* stats);

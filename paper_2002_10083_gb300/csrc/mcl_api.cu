@@ -49,6 +49,10 @@ struct mcl_ctx {
     float est_safety = 1.25f;
     int iteration = 1;
     int prev_valid = 0;
+    // Cohen's estimator
+    int cohen_r = 8;
+    uint64_t cohen_seed = 2002;
+    Buf cohen_m, cohen_e;
 };
 
 namespace {
@@ -277,7 +281,7 @@ void mcl_destroy(mcl_ctx* c) {
                   &c->flops, &c->colsum, &c->rlo, &c->rhi,  &c->cap,     &c->off,  &c->est,
                   &c->bucket, &c->work,   &c->kept,    &c->chaos,   &c->bnnz, &c->tmp_row,
                   &c->tmp_val, &c->cursors, &c->scan,  &c->ctr,     &c->active, &c->mlp_w,
-                  &c->mlp_norm, &c->colmax, &c->feats, &c->prev_logcf};
+                  &c->mlp_norm, &c->colmax, &c->feats, &c->prev_logcf, &c->cohen_m, &c->cohen_e};
     for (Buf* b : all) dev_free(c, b->p, 0);
     cudaDeviceSynchronize();
     for (auto& e : c->ev) cudaEventDestroy(e);
@@ -296,8 +300,8 @@ mcl_status mcl_get_stats(mcl_ctx* c, mcl_stats* st) {
 mcl_status mcl_set_option(mcl_ctx* c, int option, int64_t value) {
     if (!c) return MCL_ERR_INVALID;
     switch (option) {
-        case 1:  // sizing: -1 from params, 0 exact symbolic, 1 flops bound
-            if (value < -1 || value > 1) return fail(c, MCL_ERR_INVALID, "bad sizing option");
+        case 1:  // sizing: -1 from params, 0 exact symbolic, 1 flops bound, 3 Cohen
+            if (value < -1 || value > 3 || value == 2) return fail(c, MCL_ERR_INVALID, "bad sizing option");
             c->sizing = (int)value;
             return MCL_OK;
         case 2:  // numeric configuration mask
@@ -310,6 +314,13 @@ mcl_status mcl_set_option(mcl_ctx* c, int option, int64_t value) {
         case 4:  // estimate scale in thousandths (1000 = as estimated)
             if (value < 1 || value > 1000000) return fail(c, MCL_ERR_INVALID, "bad scale");
             c->est_milli = (int)value;
+            return MCL_OK;
+        case 7:  // keys per vertex of Cohen's estimator
+            if (value < 2 || value > cohen_max_r()) return fail(c, MCL_ERR_INVALID, "bad key count");
+            c->cohen_r = (int)value;
+            return MCL_OK;
+        case 8:  // seed of Cohen's keys
+            c->cohen_seed = (uint64_t)value;
             return MCL_OK;
         case 6:  // column-batch staging budget in bytes (0: one batch)
             if (value < 0) return fail(c, MCL_ERR_INVALID, "bad budget");
@@ -361,6 +372,12 @@ static mcl_status expand_impl(mcl_ctx* c, const mcl_csc* A, const mcl_params* pr
         if ((st = internal_estimate(c, A, b, s))) return st;
     } else if (sizing == 1) {
         launch_est_from_flops(Av, b, s);
+    } else if (sizing == 3) {
+        const size_t n1 = (size_t)n + 1;
+        if (!ensure(c, c->cohen_m, n1 * c->cohen_r * 4, s) || !ensure(c, c->cohen_e, n1 * 4, s))
+            return fail(c, MCL_ERR_OOM, "estimator scratch allocation failed");
+        launch_cohen(Av, c->cohen_r, c->cohen_seed, (float*)c->cohen_m.p, (float*)c->cohen_e.p, s);
+        launch_cohen_to_est((int32_t)n, (const float*)c->cohen_e.p, 1.0f, b, s);
     } else {
         launch_symbolic(Av, b, b.est, c->num_sms, grid_max, s);
         // exact counts bound each column's output: cap_j = min(cap_j, nnz_j)
@@ -795,6 +812,31 @@ mcl_status mcl_estimate(mcl_ctx* c, const mcl_csc* A, int64_t* est, void* stream
     if ((st = err_flags(c, c->hctr->err))) return st;
     b.est = est;
     return internal_estimate(c, A, b, s);
+}
+
+mcl_status mcl_cohen_estimate(mcl_ctx* c, const mcl_csc* A, int32_t keys, uint64_t seed, float* est,
+                              void* stream) {
+    if (!c) return MCL_ERR_INVALID;
+    mcl_status st;
+    if ((st = check_csc(c, A, "A"))) return st;
+    if (keys < 2 || keys > cohen_max_r())
+        return fail(c, MCL_ERR_INVALID, "keys must be in [2, %d]", cohen_max_r());
+    if (A->n > 0 && !est) return fail(c, MCL_ERR_INVALID, "est is NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    CUDA_TRY(c, cudaSetDevice(c->device));
+    if ((st = ensure_columns(c, A->n, s))) return st;
+    // validation pass: the estimate indexes by row, so a malformed A is refused first
+    ExpandBuffers b = buffers(c);
+    PruneParams pp{};
+    pp.Krec = 1;
+    CUDA_TRY(c, cudaMemsetAsync(c->ctr.p, 0, sizeof(DevCounters), s));
+    launch_colstats(view(A), pp, b, c->num_sms, s);
+    if ((st = read_counters(c, s))) return st;
+    if ((st = err_flags(c, c->hctr->err))) return st;
+    if (!ensure(c, c->cohen_m, ((size_t)A->n + 1) * keys * 4, s))
+        return fail(c, MCL_ERR_OOM, "estimator scratch allocation failed");
+    launch_cohen(view(A), keys, seed, (float*)c->cohen_m.p, est, s);
+    return check_launch(c, "cohen");
 }
 
 static void free_csc(mcl_ctx* c, mcl_csc* M, cudaStream_t s) {

@@ -153,6 +153,12 @@ void launch_adam(float* master, float* m, float* v, const float* grad, int64_t s
 void launch_logcf(int32_t n, const int64_t* flops, const int64_t* bnnz, float* logcf,
                   cudaStream_t s);
 
+// --- Cohen's estimator (mcl_cohen.cu) ---
+int cohen_max_r();
+void launch_cohen(const CscView& A, int r, uint64_t seed, float* m, float* est, cudaStream_t s);
+void launch_cohen_to_est(int32_t n, const float* e, float safety, const ExpandBuffers& b,
+                         cudaStream_t s);
+
 // --- components (mcl_cc.cu) ---
 void launch_components(const CscView& A, int32_t* labels, DevCounters* ctr, cudaStream_t s);
 

@@ -22,6 +22,8 @@ MCL_OK = 0
 STATUS = {0: "MCL_OK", 1: "MCL_ERR_INVALID", 2: "MCL_ERR_OOM", 3: "MCL_ERR_CUDA",
           4: "MCL_ERR_TIMEOUT", 5: "MCL_ERR_NOT_CONVERGED", 6: "MCL_ERR_INTERNAL"}
 OPT_SIZING, OPT_CONF_MASK, OPT_VALIDATE, OPT_EST_SCALE, OPT_ITERATION, OPT_PHASE_BUDGET = 1, 2, 3, 4, 5, 6
+OPT_COHEN_KEYS, OPT_COHEN_SEED = 7, 8
+SIZING_COHEN = 3
 SIZING_PARAMS, SIZING_EXACT, SIZING_FLOPS = -1, 0, 1
 MAX_SELECT_K = 4096
 
@@ -88,6 +90,8 @@ SIGNATURES = {
     "mcl_estimate": (ctypes.c_int, [P, ctypes.POINTER(_Csc), P, P]),
     "mcl_symbolic_noalloc": (ctypes.c_int, [ctypes.POINTER(_Csc), P, P, ctypes.c_char_p,
                                             ctypes.c_size_t, P]),
+    "mcl_cohen_estimate": (ctypes.c_int, [P, ctypes.POINTER(_Csc), ctypes.c_int32, ctypes.c_uint64,
+                                          P, P]),
 }
 MLP_NPARAM = 5378
 NFEATURES = 16
@@ -370,6 +374,14 @@ class Context:
         est = torch.empty(max(A.n, 1), dtype=torch.int64, device=A.colptr.device)
         self._check(self.lib.mcl_estimate(self.h, ctypes.byref(a), P(est.data_ptr()),
                                           _stream_ptr(stream)))
+        return est[:A.n]
+
+    def cohen_estimate(self, A: DeviceCSC, keys: int = 8, seed: int = 2002, stream=None):
+        """Cohen's estimate of nnz((AA)_*j) per column (device float32)."""
+        a = A.c()
+        est = torch.empty(max(A.n, 1), dtype=torch.float32, device=A.colptr.device)
+        self._check(self.lib.mcl_cohen_estimate(self.h, ctypes.byref(a), int(keys), int(seed),
+                                                P(est.data_ptr()), _stream_ptr(stream)))
         return est[:A.n]
 
     def stats(self) -> dict:

@@ -92,7 +92,7 @@ def test_expand_multi_range_and_splits(ctx, mask, scale):
         ctx.set_option(mcl.OPT_EST_SCALE, 1000)
 
 
-@pytest.mark.parametrize("sizing", [0, 1])
+@pytest.mark.parametrize("sizing", [0, 1, 3])
 def test_sizing_modes_same_result(ctx, sizing):
     from paper_2002_10083_gb300 import mcl
     A = synth.random_sparse(2000, 0.01, seed=9, w="lognormal").with_val32()
