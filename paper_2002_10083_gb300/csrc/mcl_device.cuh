@@ -322,19 +322,41 @@ __device__ int block_select_mass(const uint64_t* A, int na, double target, uint6
     return found;
 }
 
-// Ascending bitonic sort of s[0..P) (P a power of two) by the block.
+// Ascending sort of s[0..n) by the block (any n >= 0): the bitonic network
+// in its all-ascending form (each merge of two sorted runs starts with a
+// reversed compare, i <-> i ^ (k - 1), followed by half-cleaners).  Every
+// comparator puts the smaller key at the lower index, so positions >= n act
+// as +infinity and are simply skipped.  Ends with a barrier.
 template <int T>
-__device__ void block_bitonic_sort(uint64_t* s, int P) {
-    for (int k = 2; k <= P; k <<= 1) {
-        for (int j = k >> 1; j > 0; j >>= 1) {
-            for (int i = threadIdx.x; i < P; i += T) {
-                int ixj = i ^ j;
-                if (ixj > i) {
-                    uint64_t a = s[i], b = s[ixj];
-                    bool up = (i & k) == 0;
-                    if ((a > b) == up) {
-                        s[i] = b;
-                        s[ixj] = a;
+__device__ void block_sort_asc(uint64_t* s, int n) {
+    int P = 1, lg = 0;
+    while (P < n) {
+        P <<= 1;
+        ++lg;
+    }
+    for (int lk = 1; lk <= lg; ++lk) {
+        const int k = 1 << lk, hk = k >> 1;
+        for (int t = threadIdx.x; t < (P >> 1); t += T) {
+            const int blk = t >> (lk - 1), off = t & (hk - 1);
+            const int i = blk * k + off, j = blk * k + (k - 1 - off);
+            if (j < n) {
+                const uint64_t x = s[i], y = s[j];
+                if (x > y) {
+                    s[i] = y;
+                    s[j] = x;
+                }
+            }
+        }
+        __syncthreads();
+        for (int lj = lk - 2; lj >= 0; --lj) {
+            const int jj = 1 << lj;
+            for (int t = threadIdx.x; t < (P >> 1); t += T) {
+                const int i = ((t >> lj) << (lj + 1)) + (t & (jj - 1)), j = i + jj;
+                if (j < n) {
+                    const uint64_t x = s[i], y = s[j];
+                    if (x > y) {
+                        s[i] = y;
+                        s[j] = x;
                     }
                 }
             }

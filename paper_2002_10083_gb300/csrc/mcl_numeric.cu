@@ -1,29 +1,28 @@
 // The fused numeric pass of one MCL iteration (Algorithm 1: expansion,
-// Prune, inflation) with an order-preserving shared-memory accumulator.
+// Prune, inflation) with a shared-memory hash accumulator.
 //
 // One CTA owns one output column j at a time (persistent grid, LPT order).
-// The column's row span is processed in windows of at most WW*32 rows:
+// The column's row span is cut into row windows sized from the output-size
+// estimate so that each holds at most LIM distinct rows:
 //
-//   1. bitmap:     every product row of the window sets a bit (the exact
-//                  symbolic pass of Sections II and V, restricted to the
-//                  window);
-//   2. prefix:     block scan of the words' popcounts, so that
-//                  rank(row) = prefix[word] + popc(word & lower bits) is a
-//                  collision-free, row-order-preserving index;
-//   3. accumulate: c_ij += a_ik * a_kj (FP32) at vals[rank(i)] -- a dense
-//                  array without keys, probes or compare-and-swap;
-//   4. extract:    in row order: exact column statistics (sum, count and
-//                  mass above the threshold) and ranking keys above the
-//                  running top-k bound tau, appended stably to a row-ordered
-//                  candidate buffer, which is cut back to the top ksel
-//                  entries (radix select + stable compaction) only when full.
+//   1. insert:  every product a_ik * a_kj of the window is added into an
+//               open-addressing table (HS slots, row keys, FP32 values,
+//               linear probing; a new key is claimed by compare-and-swap and
+//               its slot appended to an entry list), so the work is
+//               proportional to the products and entries, not to the span;
+//   2. extract: over the entry list, exact column statistics (count, count
+//               and mass above the threshold) and the ranking keys above the
+//               running top-k bound tau, appended to a candidate buffer that
+//               is cut back to the top ksel keys (radix select) when full;
+//   3. clear:   the used slots only.
 //
-// A window whose entries exceed the value capacity is cut at the last
-// bitmap word that fits (counted as a split) and the next window narrows
-// to the observed density; results never depend on the size estimate.
-// Finally the prune rule picks m* (threshold / top-k / recovery), the kept
-// keys are compacted stably (so rows come out sorted without a sort),
-// inflated, renormalised with an FP64 sum and written with chaos_j.
+// Windows come from per-window product buckets (a counting pass and a
+// scatter of (row, product) into window order) or, without bucket space,
+// from per-source cursors over the sorted rows.  A window whose distinct
+// rows exceed LIM is halved and redone (counted as a split); results never
+// depend on the size estimate.  Finally the prune rule picks m* (threshold /
+// top-k / recovery), the kept keys are sorted by row, inflated, renormalised
+// with an FP64 sum and written with chaos_j.
 #include <cfloat>
 #include <climits>
 #include <cstdint>
@@ -40,8 +39,8 @@ struct WinShared {
     int wsm[34];
     int item;
     int next;
-    int cutw;
-    int pad;
+    int nent;  // entries claimed in the window's table
+    int ovf;   // the window exceeded its capacity
 };
 
 // Exclusive block scan of one int per thread; *total gets the sum.  Three
@@ -104,10 +103,9 @@ __device__ int compact_stable(uint64_t* a, int n, uint64_t cut, int* wsm) {
     return outpos;
 }
 
-// Scratch per CTA in global memory (stride = cur_stride sources):
-//   [0 .. s)      int64 start of the source column
-//   [s .. 2s)     (as int32 pairs) length, cursor
-//   ...           see SrcMeta below
+// Scratch per CTA in global memory (stride = cur_stride sources): source
+// column start (int64), length, two cursor arrays (read / write; swapped
+// after a window succeeds) and a_kj.
 struct SrcMeta {
     int64_t* ks;
     int32_t* len;
@@ -123,10 +121,11 @@ struct SrcMeta {
     }
 };
 
-// Finish a column: prune rule on the row-ordered candidate keys top[0..ntop)
-// plus exact statistics; stable output of the kept entries with inflation
-// (inflate != 0) or their B values; returns m* and chaos_j via the pointers.
-template <int T, int IPT>
+// Finish a column: prune rule on the candidate keys top[0..ntop) plus exact
+// statistics, then the kept keys in row order (sorted here unless the
+// buffer is already row-ordered) written with inflation (pp.inflate) or
+// their B values; returns m* and chaos_j via the pointers.
+template <int T, int IPT, bool ROW_ORDERED>
 __device__ void finish_column(uint64_t* top, int ntop, const PruneParams& pp, double S, double MT,
                               long long Tt, int64_t cap, int32_t* out_row, float* out_val,
                               unsigned* hist, unsigned long long* mhist, WinShared* sh, DevCounters* ctr,
@@ -188,47 +187,47 @@ __device__ void finish_column(uint64_t* top, int ntop, const PruneParams& pp, do
         else
             cut = block_select_count<T>(top, ntop, top, 0, mstar, hist, &sh->bs);
     }
-    // pass 1: per-thread kept counts and inflated sum over contiguous chunks
-    const int per = (ntop + T - 1) / T;
-    const int i0 = tid * per, i1 = min(ntop, i0 + per);
-    int c = 0;
-    double usum = 0.0;
-    if (mstar > 0) {
-        for (int i = i0; i < i1; ++i) {
-            const uint64_t x = top[i];
-            if (x >= cut) {
-                ++c;
-                if (pp.inflate) usum += (double)inflate_value(key_val(x), pp.r);
-            }
-        }
+    // the kept keys (exactly m* of them: keys are distinct) to the front
+    int m = mstar > 0 ? compact_stable<T, IPT>(top, ntop, cut, sh->wsm) : 0;
+    if (m != mstar) {
+        if (tid == 0) set_err2(ctr, ERR_INTERNAL);
+        m = m < mstar ? m : mstar;
     }
+    if (!ROW_ORDERED && m > 1) {
+        // re-key as (row, value bits) and sort ascending: rows are distinct
+        for (int i = tid; i < m; i += T) {
+            const uint64_t x = top[i];
+            top[i] = ((uint64_t)(uint32_t)key_row(x) << 32) | (x >> 32);
+        }
+        __syncthreads();
+        block_sort_asc<T>(top, m);
+        for (int i = tid; i < m; i += T) {
+            const uint64_t x = top[i];
+            top[i] = make_key(__uint_as_float((uint32_t)x), (int)(x >> 32));
+        }
+        __syncthreads();
+    }
+    double usum = 0.0;
+    if (pp.inflate)
+        for (int i = tid; i < m; i += T) usum += (double)inflate_value(key_val(top[i]), pp.r);
     double dv[1] = {usum};
     long long qv[1] = {0};
     block_sum<T>(dv, 1, qv, 0, &sh->bs);
     const double U = dv[0];
     const double invU = U > 0.0 ? 1.0 / U : 0.0;
-    int tot;
-    int o = block_scan_excl<T>(c, &tot, sh->wsm);
-    if (tid == 0 && tot != mstar) set_err2(ctr, ERR_INTERNAL);
     double amax = 0.0, asq = 0.0;
-    if (mstar > 0) {
-        for (int i = i0; i < i1; ++i) {
-            const uint64_t x = top[i];
-            if (x >= cut) {
-                if (o >= mstar) break;
-                const float v = key_val(x);
-                float outv = v;
-                if (pp.inflate) {
-                    const double a = (double)inflate_value(v, pp.r) * invU;
-                    outv = (float)a;
-                    amax = a > amax ? a : amax;
-                    asq += a * a;
-                }
-                out_row[o] = key_row(x);
-                out_val[o] = outv;
-                ++o;
-            }
+    for (int i = tid; i < m; i += T) {
+        const uint64_t x = top[i];
+        const float v = key_val(x);
+        float outv = v;
+        if (pp.inflate) {
+            const double a = (double)inflate_value(v, pp.r) * invU;
+            outv = (float)a;
+            amax = a > amax ? a : amax;
+            asq += a * a;
         }
+        out_row[i] = key_row(x);
+        out_val[i] = outv;
     }
     double ch = 0.0;
     if (pp.inflate) {
@@ -239,17 +238,16 @@ __device__ void finish_column(uint64_t* top, int ntop, const PruneParams& pp, do
         if (ch < 0.0) ch = 0.0;
     }
     if (tid == 0) {
-        *mstar_out = mstar;
+        *mstar_out = m;
         *chaos_out = ch;
     }
     __syncthreads();
 }
 
-// Append the candidates an enumerator yields (stably, in its order) to the
-// row-ordered buffer top[0..ntop); first cuts the buffer back to ksel
-// entries if they would not fit.  `count(tau)` returns this thread's number
-// of keys > tau; `emit(tau, dst, base)` writes every thread's keys in the
-// enumerator's stable order, given each thread's exclusive scan offset.
+// Append the candidates an enumerator yields to top[0..ntop); first cuts
+// the buffer back to ksel entries if they would not fit.  `count(tau)`
+// returns this thread's number of keys > tau; `emit(tau, dst, base)` writes
+// this thread's keys at dst[base ...] (base: its exclusive scan offset).
 template <int T, int IPT, class Enum>
 __device__ __forceinline__ void append_candidates(Enum& en, uint64_t* top, int topcap, int ksel,
                                                   int& ntop, uint64_t& tau, int c, unsigned* hist,
@@ -269,73 +267,83 @@ __device__ __forceinline__ void append_candidates(Enum& en, uint64_t* top, int t
     __syncthreads();
 }
 
-// Enumerates a window's entries (bitmap + prefix + dense values).  Warp w
-// owns words [w*wpw, (w+1)*wpw); lane l takes words w*wpw + 32q + l, so
-// shared-memory accesses are conflict-free and the stable (row) order is
-// round q, then lane.
-struct WindowEnum {
-    const uint32_t* bm;
-    const int32_t* pre;
-    const float* vals;
-    int nw, wpw, r0;
-    __device__ int word(int q) const { return (threadIdx.x >> 5) * wpw + 32 * q + (threadIdx.x & 31); }
+// The entries of a window's table, enumerated through its entry list
+// (thread t takes entries t, t + T, ...).
+template <int T>
+struct TableEnum {
+    const int* hkey;
+    const float* hval;
+    const uint16_t* elist;
+    int nent;
     __device__ int count(uint64_t tau) const {
         int c = 0;
-        for (int q = 0; q < wpw / 32; ++q) {
-            const int w = word(q);
-            if (w >= nw) break;
-            uint32_t m = bm[w];
-            int r = pre[w];
-            while (m) {
-                const int b = __ffs(m) - 1;
-                m &= m - 1;
-                if (make_key(vals[r], r0 + 32 * w + b) > tau) ++c;
-                ++r;
-            }
+        for (int e = threadIdx.x; e < nent; e += T) {
+            const int h = elist[e];
+            c += make_key(hval[h], hkey[h]) > tau;
         }
         return c;
     }
-    // base: this thread's exclusive block-scan offset of count()
     __device__ void emit(uint64_t tau, uint64_t* dst, int base) const {
-        const int lane = threadIdx.x & 31;
-        int run = __shfl_sync(FULL, base, 0);  // the warp's first output slot
-        for (int q = 0; q < wpw / 32; ++q) {
-            const int w = word(q);
-            int c = 0;
-            uint32_t m0 = 0;
-            int r0w = 0;
-            if (w < nw) {
-                m0 = bm[w];
-                r0w = pre[w];
-                uint32_t m = m0;
-                int r = r0w;
-                while (m) {
-                    const int b = __ffs(m) - 1;
-                    m &= m - 1;
-                    if (make_key(vals[r], r0 + 32 * w + b) > tau) ++c;
-                    ++r;
-                }
-            }
-            int incl = c;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int y = __shfl_up_sync(FULL, incl, o);
-                if (lane >= o) incl += y;
-            }
-            int pos = run + incl - c;
-            uint32_t m = m0;
-            int r = r0w;
-            while (m) {
-                const int b = __ffs(m) - 1;
-                m &= m - 1;
-                const uint64_t key = make_key(vals[r], r0 + 32 * w + b);
-                if (key > tau) dst[pos++] = key;
-                ++r;
-            }
-            run += __shfl_sync(FULL, incl, 31);
+        for (int e = threadIdx.x; e < nent; e += T) {
+            const int h = elist[e];
+            const uint64_t k = make_key(hval[h], hkey[h]);
+            if (k > tau) dst[base++] = k;
         }
     }
 };
+
+constexpr int HEMPTY = -1;
+
+// Add product v at row into the window's table; called by all 32 lanes
+// (valid marks the lanes that carry a product).  New keys are claimed by
+// compare-and-swap and their slots appended (warp-aggregated) to the entry
+// list; more than LIM entries, or a probe run over the whole table, marks
+// the window as overflowed (its products are then redone in halves).
+template <int HS, int LIM, int ELCAP>
+__device__ __forceinline__ void table_add(bool valid, int row, float v, int* hkey, float* hval,
+                                          uint16_t* elist, WinShared* sh) {
+    constexpr int LOGHS = HS == 1024 ? 10 : HS == 2048 ? 11 : HS == 4096 ? 12 : HS == 8192 ? 13 : 0;
+    static_assert(LOGHS > 0, "table size");
+    int h = 0;
+    bool isnew = false;
+    if (valid) {
+        h = (int)(((uint32_t)row * 0x9E3779B1u) >> (32 - LOGHS));
+        for (int probes = 0;; ++probes) {
+            const int k = *(volatile int*)(hkey + h);
+            if (k == row) break;
+            if (k == HEMPTY) {
+                const int old = atomicCAS(hkey + h, HEMPTY, row);
+                if (old == HEMPTY) {
+                    isnew = true;
+                    break;
+                }
+                if (old == row) break;
+            }
+            h = (h + 1) & (HS - 1);
+            if (probes >= HS) {
+                valid = false;
+                sh->ovf = 1;
+                break;
+            }
+        }
+        if (valid) atomicAdd(hval + h, v);
+    }
+    const unsigned nm = __ballot_sync(FULL, isnew);
+    if (nm) {
+        const int lane = threadIdx.x & 31;
+        const int leader = __ffs(nm) - 1;
+        int base = 0;
+        if (lane == leader) {
+            base = atomicAdd(&sh->nent, __popc(nm));
+            if (base + __popc(nm) > LIM) sh->ovf = 1;
+        }
+        base = __shfl_sync(FULL, base, leader);
+        if (isnew) {
+            const int e = base + __popc(nm & lanemask_lt());
+            if (e < ELCAP) elist[e] = (uint16_t)h;
+        }
+    }
+}
 
 // Expected entries per source and window below which a window walks its
 // sources one per lane instead of one per warp.
@@ -348,11 +356,12 @@ struct ExpandArgs {
     int conf;
 };
 
-template <int T, int WW, int VC>
+template <int T, int HS, int LIM>
 struct ExpandLayout {
+    static constexpr int ELCAP = LIM + 32;
     static constexpr size_t bytes(int ksel) {
-        return (size_t)WW * 4 + (size_t)WW * 4 + (size_t)VC * 4 + (size_t)(ksel + VC) * 8 +
-               256 * 4 + 256 * 8 + sizeof(WinShared);
+        return (size_t)HS * 8 + (size_t)(ksel + LIM) * 8 + 256 * 4 + 256 * 8 + sizeof(WinShared) +
+               (size_t)ELCAP * 2;
     }
 };
 
@@ -375,23 +384,23 @@ struct FastDiv {
     }
 };
 
-template <int T, int WW, int VC, int MINB>
+template <int T, int HS, int LIM, int MINB>
 __global__ void __launch_bounds__(T, MINB) k_expand(ExpandArgs a) {
-    constexpr int WROWS = WW * 32;
     constexpr int IPT = 8;
-    constexpr int NWARP = T / 32;
+    constexpr int ELCAP = ExpandLayout<T, HS, LIM>::ELCAP;
+    constexpr int TGT = LIM * 3 / 4;  // planned entries per window
     extern __shared__ __align__(16) unsigned char smem[];
-    uint32_t* bm = reinterpret_cast<uint32_t*>(smem);
-    int32_t* pre = reinterpret_cast<int32_t*>(bm + WW);
-    float* vals = reinterpret_cast<float*>(pre + WW);
-    uint64_t* top = reinterpret_cast<uint64_t*>(vals + VC);
+    int* hkey = reinterpret_cast<int*>(smem);
+    float* hval = reinterpret_cast<float*>(hkey + HS);
+    uint64_t* top = reinterpret_cast<uint64_t*>(hval + HS);
     const int ksel = a.pp.ksel;
-    const int topcap = ksel + VC;
+    const int topcap = ksel + LIM;
     unsigned* hist = reinterpret_cast<unsigned*>(top + topcap);
     unsigned long long* mhist = reinterpret_cast<unsigned long long*>(hist + 256);
     WinShared* sh = reinterpret_cast<WinShared*>(mhist + 256);
+    uint16_t* elist = reinterpret_cast<uint16_t*>(sh + 1);
 
-    const int tid = threadIdx.x, lane = tid & 31;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const CscView& A = a.A;
     const ExpandBuffers& b = a.b;
     DevCounters* ctr = b.ctr;
@@ -401,6 +410,10 @@ __global__ void __launch_bounds__(T, MINB) k_expand(ExpandArgs a) {
     int32_t* woff = b.woff ? b.woff + (int64_t)blockIdx.x * (WINDOW_MAX + 1) : nullptr;
     const int wbeg = ctr->bin_off[a.conf * NZ], wend = ctr->bin_off[a.conf * NZ + NZ];
 
+    for (int i = tid; i < HS; i += T) {
+        hkey[i] = HEMPTY;
+        hval[i] = 0.0f;
+    }
     for (;;) {
         if (tid == 0) sh->item = atomicAdd(&ctr->conf_ctr[a.conf], 1);
         __syncthreads();
@@ -445,20 +458,18 @@ __global__ void __launch_bounds__(T, MINB) k_expand(ExpandArgs a) {
             meta.akj[i] = akj;
             s_sum += (double)akj * b.colsum[k];
         }
-        // ---- plan: one window, bucketed windows, or source-cursor windows ----
-        int nwin = 1, width = span;
+        // ---- plan: windows of equal row width holding ~TGT entries each ----
+        int64_t nw64 = (est + TGT - 1) / TGT;
+        if (nw64 < 1) nw64 = 1;
+        if (nw64 > span) nw64 = span;
         bool bucket = false;
-        const bool single = span <= WROWS && est * 4 <= (int64_t)VC * 3;
-        if (!single && brow != nullptr && flops_j <= b.bucket_cap) {
-            const int64_t nw1 = ((int64_t)span + WROWS - 1) / WROWS;
-            const int64_t nw2 = (est * 4 + (int64_t)VC * 3 - 1) / ((int64_t)VC * 3);
-            const int64_t nwr = nw1 > nw2 ? nw1 : nw2;
-            if (nwr <= (WINDOW_MAX < WW ? WINDOW_MAX : WW)) {
-                width = (int)((((int64_t)span + nwr - 1) / nwr + 31) & ~31ll);
-                nwin = (int)(((int64_t)span + width - 1) / width);
-                bucket = true;
-            }
+        if (nw64 > 1 && brow != nullptr && flops_j <= b.bucket_cap) {
+            const int64_t wmax = WINDOW_MAX < HS ? WINDOW_MAX : HS;
+            if (nw64 > wmax) nw64 = wmax;
+            bucket = true;
         }
+        int width = (int)(((int64_t)span + nw64 - 1) / nw64);
+        const int nwin = (int)(((int64_t)span + width - 1) / width);
         int ntop = 0;
         uint64_t tau = 0;
         double s_mt = 0.0;
@@ -468,8 +479,9 @@ __global__ void __launch_bounds__(T, MINB) k_expand(ExpandArgs a) {
         __syncthreads();
 
         if (bucket) {
-            // ---- count the products of every window ----
-            int* wcnt = reinterpret_cast<int*>(bm);
+            // ---- count the products of every window (counters in the table's key array) ----
+            int* wcnt = hkey;
+            int* wcur = reinterpret_cast<int*>(hval);
             for (int i = tid; i < nwin; i += T) wcnt[i] = 0;
             if (tid == 0) sh->next = 0;
             __syncthreads();
@@ -500,7 +512,7 @@ __global__ void __launch_bounds__(T, MINB) k_expand(ExpandArgs a) {
                 }
             }
             __syncthreads();
-            // ---- window offsets (exclusive scan), scatter cursors in pre ----
+            // ---- window offsets (exclusive scan), scatter cursors ----
             {
                 const int per = (nwin + T - 1) / T;
                 const int i0 = min(nwin, tid * per), i1 = min(nwin, i0 + per);
@@ -510,7 +522,7 @@ __global__ void __launch_bounds__(T, MINB) k_expand(ExpandArgs a) {
                 int run = block_scan_excl<T>(c, &tot, sh->wsm);
                 for (int i = i0; i < i1; ++i) {
                     woff[i] = run;
-                    pre[i] = run;
+                    wcur[i] = run;
                     run += wcnt[i];
                 }
                 if (tid == 0) woff[nwin] = tot;
@@ -540,91 +552,98 @@ __global__ void __launch_bounds__(T, MINB) k_expand(ExpandArgs a) {
                     }
 #pragma unroll
                     for (int c = 0; c < 4; ++c) {
-                    const bool v = pb + 32 * c + lane < len;
-                    const unsigned act = __ballot_sync(FULL, v);
-                    if (v) {
-                        const int row = rr[c];
-                        const float prod = pv[c] * akj;
-                        const uint32_t w = fdiv.div((uint32_t)(row - lo));
-                        const unsigned grp = __match_any_sync(act, w);
-                        const int leader = __ffs(grp) - 1;
-                        int base = 0;
-                        if (lane == leader) base = atomicAdd(pre + w, __popc(grp));
-                        base = __shfl_sync(grp, base, leader);
-                        const int pos = base + __popc(grp & lanemask_lt());
-                        brow[pos] = row;
-                        bval[pos] = prod;
-                    }
+                        const bool v = pb + 32 * c + lane < len;
+                        const unsigned act = __ballot_sync(FULL, v);
+                        if (v) {
+                            const int row = rr[c];
+                            const float prod = pv[c] * akj;
+                            const uint32_t w = fdiv.div((uint32_t)(row - lo));
+                            const unsigned grp = __match_any_sync(act, w);
+                            const int leader = __ffs(grp) - 1;
+                            int base = 0;
+                            if (lane == leader) base = atomicAdd(wcur + w, __popc(grp));
+                            base = __shfl_sync(grp, base, leader);
+                            const int pos = base + __popc(grp & lanemask_lt());
+                            brow[pos] = row;
+                            bval[pos] = prod;
+                        }
                     }
                 }
             }
             __syncthreads();
+            for (int i = tid; i < nwin; i += T) {
+                hkey[i] = HEMPTY;
+                hval[i] = 0.0f;
+            }
         }
 
-        int wrows;
-        {
-            const double rows = 0.8 * (double)VC * (double)span / (double)est;
-            wrows = rows >= (double)WROWS ? WROWS : (int)rows;
-            wrows &= ~31;
-            if (wrows < 32) wrows = 32;
-            if (single) wrows = ((span + 31) & ~31) < WROWS ? ((span + 31) & ~31) : WROWS;
-        }
-        int r0 = lo;
+        // ---- windows: [r0, r1) inside window `win` = [lo + win*width, wr1) ----
         int win = 0;
-        int bs0 = 0, be0 = 0, wend_row = hiE;
-        if (bucket) {
-            bs0 = woff[0];
-            be0 = woff[1];
-            wend_row = min(hiE, lo + width);
-        }
+        int r0 = lo;
+        int wr1 = (int)min((int64_t)lo + width, (int64_t)hiE);
+        int r1 = wr1;
+        int32_t* cur = meta.cur;
+        int32_t* nxt = meta.nxt;
+        const bool lane_mode =
+            !bucket && (double)flops_j * (double)width < (double)LANE_MODE_MAX * (double)d * (double)span;
         while (r0 < hiE) {
-            int r1;
-            if (bucket) {
-                if (r0 >= wend_row) {  // next bucket window
-                    ++win;
-                    bs0 = woff[win];
-                    be0 = woff[win + 1];
-                    wend_row = (int)min((int64_t)lo + (int64_t)(win + 1) * width, (int64_t)hiE);
-                    r0 = (int)((int64_t)lo + (int64_t)win * width);
-                    if (be0 == bs0) {  // empty window
-                        r0 = wend_row;
-                        continue;
-                    }
-                }
-                r1 = wend_row;
-                if (r1 - r0 > WROWS) r1 = r0 + WROWS;
-            } else {
-                r1 = (int)min((int64_t)r0 + wrows, (int64_t)hiE);
+            if (tid == 0) {
+                sh->nent = 0;
+                sh->ovf = 0;
+                sh->next = 0;
             }
-            const int nw = (r1 - r0 + 31) >> 5;
-            // ---- 1. bitmap of the window's product rows ----
-            for (int i = tid; i < nw; i += T) bm[i] = 0u;
-            if (tid == 0) sh->next = 0;
-            const bool lane_mode = !bucket && (double)flops_j * (double)(r1 - r0) <
-                                                  (double)LANE_MODE_MAX * (double)d * (double)span;
             __syncthreads();
+            // ---- 1. insert the products of rows [r0, r1) ----
             if (bucket) {
-#pragma unroll 4
-                for (int p = bs0 + tid; p < be0; p += T) {
-                    const int r = brow[p];
-                    if (r >= r0 && r < r1) {
-                        const int off = r - r0;
-                        atomicOr(bm + (off >> 5), 1u << (off & 31));
+                const int bs = woff[win], be = woff[win + 1];
+                const bool filt = r0 != lo + win * width || r1 != wr1;
+                for (int pb = bs + warp * 32; pb < be; pb += T) {
+                    const int p = pb + lane;
+                    bool valid = p < be;
+                    int row = 0;
+                    float v = 0.0f;
+                    if (valid) {
+                        row = brow[p];
+                        v = bval[p];
+                        if (filt) valid = row >= r0 && row < r1;
                     }
+                    table_add<HS, LIM, ELCAP>(valid, row, v, hkey, hval, elist, sh);
                 }
             } else if (lane_mode) {
-                for (int kidx = tid; kidx < d; kidx += T) {
-                    const int len = meta.len[kidx];
-                    const int32_t* rows = A.rowidx + meta.ks[kidx];
-                    int pos = meta.cur[kidx];
-                    while (pos < len) {
-                        const int r = __ldg(rows + pos);
-                        if (r >= r1) break;
-                        const int off = r - r0;
-                        atomicOr(bm + (off >> 5), 1u << (off & 31));
-                        ++pos;
+                for (int kb = warp * 32; kb < d; kb += T) {
+                    const int kidx = kb + lane;
+                    int len = 0, pos = 0;
+                    const int32_t* rows = nullptr;
+                    const float* vv = nullptr;
+                    float akj = 0.0f;
+                    bool more = kidx < d;
+                    if (more) {
+                        const int64_t ks = meta.ks[kidx];
+                        rows = A.rowidx + ks;
+                        vv = A.val + ks;
+                        len = meta.len[kidx];
+                        akj = meta.akj[kidx];
+                        pos = cur[kidx];
                     }
-                    meta.nxt[kidx] = pos;
+                    while (__any_sync(FULL, more)) {
+                        bool valid = false;
+                        int row = 0;
+                        float v = 0.0f;
+                        if (more) {
+                            if (pos < len) {
+                                row = __ldg(rows + pos);
+                                valid = row < r1;
+                            }
+                            if (valid) {
+                                v = __ldg(vv + pos) * akj;
+                                ++pos;
+                            } else {
+                                more = false;
+                            }
+                        }
+                        table_add<HS, LIM, ELCAP>(valid, row, v, hkey, hval, elist, sh);
+                    }
+                    if (kidx < d) nxt[kidx] = pos;
                 }
             } else {
                 for (;;) {
@@ -632,192 +651,75 @@ __global__ void __launch_bounds__(T, MINB) k_expand(ExpandArgs a) {
                     if (lane == 0) kidx = atomicAdd(&sh->next, 1);
                     kidx = __shfl_sync(FULL, kidx, 0);
                     if (kidx >= d) break;
+                    const int64_t ks = meta.ks[kidx];
+                    const int32_t* rows = A.rowidx + ks;
+                    const float* vv = A.val + ks;
+                    const float akj = meta.akj[kidx];
                     const int len = meta.len[kidx];
-                    const int32_t* rows = A.rowidx + meta.ks[kidx];
-                    int pos = meta.cur[kidx];
+                    int pos = cur[kidx];
                     while (pos < len) {
-                        int rr[4];
-#pragma unroll
-                        for (int c = 0; c < 4; ++c) {
-                            const int p = pos + 32 * c + lane;
-                            rr[c] = p < len ? __ldg(rows + p) : INT_MAX;
-                        }
-                        int consumed = 0;
-                        bool stop = false;
-#pragma unroll
-                        for (int c = 0; c < 4; ++c) {
-                            if (!stop) {
-                                const bool in = rr[c] < r1;
-                                const unsigned bal = __ballot_sync(FULL, in);
-                                if (in) {
-                                    const int off = rr[c] - r0;
-                                    atomicOr(bm + (off >> 5), 1u << (off & 31));
-                                }
-                                const int nin = __popc(bal);
-                                consumed += nin;
-                                stop = nin < 32;
-                            }
-                        }
-                        pos += consumed;
-                        if (stop) break;
+                        const int p = pos + lane;
+                        const int row = p < len ? __ldg(rows + p) : INT_MAX;
+                        const bool valid = row < r1;
+                        const float v = valid ? __ldg(vv + p) * akj : 0.0f;
+                        table_add<HS, LIM, ELCAP>(valid, row, v, hkey, hval, elist, sh);
+                        const int nin = __popc(__ballot_sync(FULL, valid));
+                        pos += nin;
+                        if (nin < 32) break;
                     }
-                    if (lane == 0) meta.nxt[kidx] = pos;
+                    if (lane == 0) nxt[kidx] = pos;
                 }
             }
             __syncthreads();
-            // ---- 2. prefix of popcounts: warp-contiguous, lane-interleaved words ----
-            const int wpw = ((nw + NWARP * 32 - 1) / (NWARP * 32)) * 32;
-            const int wbase = (tid >> 5) * wpw;
-            int cnt = 0;
-            for (int q = 0; q < wpw / 32; ++q) {
-                const int w = wbase + 32 * q + lane;
-                if (w < nw) cnt += __popc(bm[w]);
-            }
-            int total;
-            int run = block_scan_excl<T>(cnt, &total, sh->wsm);
-            run = __shfl_sync(FULL, run, 0);
-            for (int q = 0; q < wpw / 32; ++q) {
-                const int w = wbase + 32 * q + lane;
-                const int c1 = w < nw ? __popc(bm[w]) : 0;
-                int incl = c1;
-#pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const int y = __shfl_up_sync(FULL, incl, o);
-                    if (lane >= o) incl += y;
+            const int nent = sh->nent;
+            if (sh->ovf || nent > LIM) {
+                // halve the range and redo it (a single row never overflows)
+                for (int i = tid; i < HS; i += T) {
+                    hkey[i] = HEMPTY;
+                    hval[i] = 0.0f;
                 }
-                if (w < nw) pre[w] = run + incl - c1;
-                run += __shfl_sync(FULL, incl, 31);
-            }
-            int r1c = r1, nwc = nw, Nw = total;
-            const bool ovf = total > VC;
-            if (ovf) {
-                // cut at the first word whose entries would not fit
-                if (tid == 0) sh->cutw = nw;
-                __syncthreads();
-                for (int q = 0; q < wpw / 32; ++q) {
-                    const int w = wbase + 32 * q + lane;
-                    if (w < nw) {
-                        const int p0 = pre[w];
-                        if (p0 <= VC && p0 + __popc(bm[w]) > VC) sh->cutw = w;
-                    }
-                }
-                __syncthreads();
-                nwc = sh->cutw;  // >= 1: one word holds at most 32 <= VC entries
-                r1c = r0 + 32 * nwc;
-                Nw = pre[nwc];
-                wrows = max(32, 32 * nwc);
                 if (tid == 0) atomicAdd(&ctr->splits, 1ull);
+                r1 = r0 + (r1 - r0) / 2;
+                __syncthreads();
+                continue;
             }
-            // ---- 3. accumulate c_ij at vals[rank(i)] ----
-            for (int i = tid; i < Nw; i += T) vals[i] = 0.0f;
-            if (tid == 0) sh->next = 0;
-            __syncthreads();
-            if (bucket) {
-#pragma unroll 4
-                for (int p = bs0 + tid; p < be0; p += T) {
-                    const int r = brow[p];
-                    if (r >= r0 && r < r1c) {
-                        const int off = r - r0;
-                        const int w = off >> 5;
-                        const int rk = pre[w] + __popc(bm[w] & ((1u << (off & 31)) - 1u));
-                        atomicAdd(vals + rk, bval[p]);
-                    }
-                }
-            } else if (lane_mode) {
-                for (int kidx = tid; kidx < d; kidx += T) {
-                    const int64_t ks = meta.ks[kidx];
-                    const int32_t* rows = A.rowidx + ks;
-                    const float* vv = A.val + ks;
-                    const float akj = meta.akj[kidx];
-                    const int end = meta.nxt[kidx];
-                    int p = meta.cur[kidx];
-                    for (; p < end; ++p) {
-                        const int row = __ldg(rows + p);
-                        if (row >= r1c) break;
-                        const int off = row - r0;
-                        const int w = off >> 5;
-                        const int rk = pre[w] + __popc(bm[w] & ((1u << (off & 31)) - 1u));
-                        atomicAdd(vals + rk, __ldg(vv + p) * akj);
-                    }
-                    meta.cur[kidx] = p;
-                }
-            } else {
-                for (;;) {
-                    int kidx = 0;
-                    if (lane == 0) kidx = atomicAdd(&sh->next, 1);
-                    kidx = __shfl_sync(FULL, kidx, 0);
-                    if (kidx >= d) break;
-                    const int64_t ks = meta.ks[kidx];
-                    const int32_t* rows = A.rowidx + ks;
-                    const float* vv = A.val + ks;
-                    const float akj = meta.akj[kidx];
-                    const int pos = meta.cur[kidx];
-                    const int end = meta.nxt[kidx];
-                    if (!ovf) {
-#pragma unroll 4
-                        for (int p = pos + lane; p < end; p += 32) {
-                            const int off = __ldg(rows + p) - r0;
-                            const float v = __ldg(vv + p) * akj;
-                            const int w = off >> 5;
-                            const int rk = pre[w] + __popc(bm[w] & ((1u << (off & 31)) - 1u));
-                            atomicAdd(vals + rk, v);
-                        }
-                        if (lane == 0) meta.cur[kidx] = end;
-                    } else {
-                        int used = 0;
-                        for (int pb = pos; pb < end; pb += 32) {
-                            const int p = pb + lane;
-                            int row = INT_MAX;
-                            if (p < end) row = __ldg(rows + p);
-                            const bool in = row < r1c;
-                            used += __popc(__ballot_sync(FULL, in));
-                            if (in) {
-                                const int off = row - r0;
-                                const float v = __ldg(vv + p) * akj;
-                                const int w = off >> 5;
-                                const int rk = pre[w] + __popc(bm[w] & ((1u << (off & 31)) - 1u));
-                                atomicAdd(vals + rk, v);
-                            }
-                        }
-                        if (lane == 0) meta.cur[kidx] = pos + used;
-                    }
-                }
-            }
-            __syncthreads();
-            // ---- 4. statistics and candidates, in row order ----
-            const int wpw2 = ((nwc + NWARP * 32 - 1) / (NWARP * 32)) * 32;
-            WindowEnum en{bm, pre, vals, nwc, wpw2, r0};
+            // ---- 2. statistics and candidates ----
+            TableEnum<T> en{hkey, hval, elist, nent};
             int c = 0;
-            for (int q = 0; q < wpw2 / 32; ++q) {
-                const int w = en.word(q);
-                if (w >= nwc) break;
-                uint32_t m = bm[w];
-                int r = pre[w];
-                s_n += __popc(m);
-                while (m) {
-                    const int bb = __ffs(m) - 1;
-                    m &= m - 1;
-                    const float v = vals[r];
-                    ++r;
-                    if (v >= a.pp.theta) {
-                        ++s_t;
-                        s_mt += (double)v;
-                    }
-                    if (make_key(v, r0 + 32 * w + bb) > tau) ++c;
+            float pmt = 0.0f;  // <= ceil(LIM / T) terms per thread and window
+            for (int e = tid; e < nent; e += T) {
+                const int h = elist[e];
+                const float v = hval[h];
+                if (v >= a.pp.theta) {
+                    ++s_t;
+                    pmt += v;
                 }
+                c += make_key(v, hkey[h]) > tau;
             }
+            if (tid == 0) s_n += nent;
+            s_mt += (double)pmt;
             append_candidates<T, IPT>(en, top, topcap, ksel, ntop, tau, c, hist, sh);
-            const int width_done = r1c - r0;
-            r0 = r1c;
-            if (!ovf && !bucket) {
-                // next window from the observed density
-                const double dens = (double)max(Nw, 1) / (double)width_done;
-                const double rows = 0.8 * (double)VC / dens;
-                int nwr = rows >= (double)WROWS ? WROWS : (int)rows;
-                nwr &= ~31;
-                if (nwr > 2 * wrows) nwr = 2 * wrows;
-                wrows = nwr < 32 ? 32 : nwr;
+            // ---- 3. clear the used slots ----
+            for (int e = tid; e < nent; e += T) {
+                const int h = elist[e];
+                hkey[h] = HEMPTY;
+                hval[h] = 0.0f;
             }
+            if (!bucket) {  // cursors advance past the window
+                int32_t* t = cur;
+                cur = nxt;
+                nxt = t;
+            }
+            r0 = r1;
+            if (r0 >= wr1) {
+                ++win;
+                if (bucket)
+                    while (win < nwin && woff[win + 1] == woff[win]) ++win;  // empty windows
+                r0 = (int)min((int64_t)lo + (int64_t)win * width, (int64_t)hiE);
+                wr1 = (int)min((int64_t)r0 + width, (int64_t)hiE);
+            }
+            r1 = wr1;
+            __syncthreads();
         }
         double dv[2] = {s_sum, s_mt};
         long long qv[2] = {s_t, s_n};
@@ -825,9 +727,10 @@ __global__ void __launch_bounds__(T, MINB) k_expand(ExpandArgs a) {
         int mstar = 0;
         double ch = 0.0;
         const int64_t obase = b.off[j];
-        finish_column<T, IPT>(top, ntop, a.pp, dv[0], dv[1], qv[0], b.cap[j],
-                              b.tmp_row + (obase - b.tmp_off0), b.tmp_val + (obase - b.tmp_off0),
-                              hist, mhist, sh, ctr, &mstar, &ch);
+        finish_column<T, IPT, false>(top, ntop, a.pp, dv[0], dv[1], qv[0], b.cap[j],
+                                     b.tmp_row + (obase - b.tmp_off0),
+                                     b.tmp_val + (obase - b.tmp_off0), hist, mhist, sh, ctr,
+                                     &mstar, &ch);
         if (tid == 0) {
             b.kept[j] = mstar;
             b.chaos[j] = ch;
@@ -837,13 +740,14 @@ __global__ void __launch_bounds__(T, MINB) k_expand(ExpandArgs a) {
     }
 }
 
-// configurations: 0 = small columns, 1 = everything else
-#define CONF0 128, 512, 1024, 6
-#define CONF1 256, 2048, 2048, 4
+// configurations: 0 = small columns, 1 = everything else (threads, table
+// slots, entries per window, CTAs per SM)
+#define CONF0 128, 1024, 512, 8
+#define CONF1 256, 2048, 1024, 4
 
 size_t numeric_smem(int conf, int ksel) {
-    return conf == 0 ? ExpandLayout<128, 512, 1024>::bytes(ksel)
-                     : ExpandLayout<256, 2048, 2048>::bytes(ksel);
+    return conf == 0 ? ExpandLayout<128, 1024, 512>::bytes(ksel)
+                     : ExpandLayout<256, 2048, 1024>::bytes(ksel);
 }
 
 int numeric_threads(int conf) { return conf == 0 ? 128 : 256; }
@@ -862,8 +766,8 @@ int numeric_grid(int conf, int ksel, int num_sms) {
     return occ * num_sms;
 }
 
-// capacity of a window's values per configuration (for binning)
-int conf_value_capacity(int conf) { return conf == 0 ? 1024 : 2048; }
+// distinct rows one window of each configuration holds (for binning)
+int conf_value_capacity(int conf) { return conf == 0 ? 512 : 1024; }
 
 void launch_numeric(int conf, const CscView& A, const PruneParams& pp, const ExpandBuffers& b,
                     int grid, cudaStream_t s) {
@@ -952,9 +856,10 @@ __global__ void __launch_bounds__(PR_T) k_prune(PruneArgs2 a) {
         int mstar = 0;
         double ch = 0.0;
         const int64_t obase = b.off[j];
-        finish_column<PR_T, 8>(top, ntop, a.pp, dv[0], dv[1], qv[0], b.cap[j],
-                               b.tmp_row + (obase - b.tmp_off0), b.tmp_val + (obase - b.tmp_off0),
-                               hist, mhist, sh, b.ctr, &mstar, &ch);
+        finish_column<PR_T, 8, true>(top, ntop, a.pp, dv[0], dv[1], qv[0], b.cap[j],
+                                     b.tmp_row + (obase - b.tmp_off0),
+                                     b.tmp_val + (obase - b.tmp_off0), hist, mhist, sh, b.ctr,
+                                     &mstar, &ch);
         if (tid == 0) {
             b.kept[j] = mstar;
             b.chaos[j] = ch;
