@@ -3,23 +3,23 @@
 //
 // One CTA owns one output column j at a time (persistent grid, LPT order).
 // The column's row span is cut into row windows sized from the output-size
-// estimate so that each holds at most LIM distinct rows:
+// estimate so that each holds about PLAN distinct rows (a table load near
+// 3/8):
 //
 //   1. insert:  every product a_ik * a_kj of the window is added into an
-//               open-addressing table (HS slots, row keys, FP32 values,
-//               linear probing; a new key is claimed by compare-and-swap and
-//               its slot appended to an entry list), so the work is
-//               proportional to the products and entries, not to the span;
-//   2. extract: over the entry list, exact column statistics (count, count
-//               and mass above the threshold) and the ranking keys above the
+//               open-addressing table (HS slots, row keys claimed by
+//               compare-and-swap, FP32 values, linear probing), so the work
+//               is proportional to the products, not to the row span;
+//   2. extract: over the table, exact column statistics (count, count and
+//               mass above the threshold) and the ranking keys above the
 //               running top-k bound tau, appended to a candidate buffer that
 //               is cut back to the top ksel keys (radix select) when full;
-//   3. clear:   the used slots only.
+//   3. clear:   the table.
 //
 // Windows come from per-window product buckets (a counting pass and a
 // scatter of (row, product) into window order) or, without bucket space,
-// from per-source cursors over the sorted rows.  A window whose distinct
-// rows exceed LIM is halved and redone (counted as a split); results never
+// from per-source cursors over the sorted rows.  A window whose probe runs
+// exceed PMAX slots is halved and redone (counted as a split); results never
 // depend on the size estimate.  Finally the prune rule picks m* (threshold /
 // top-k / recovery), the kept keys are sorted by row, inflated, renormalised
 // with an FP64 sum and written with chaos_j.
@@ -39,8 +39,8 @@ struct WinShared {
     int wsm[34];
     int item;
     int next;
-    int nent;  // entries claimed in the window's table
-    int ovf;   // the window exceeded its capacity
+    int pad;
+    int ovf;  // the window exceeded its table
 };
 
 // Exclusive block scan of one int per thread; *total gets the sum.  Three
@@ -267,81 +267,53 @@ __device__ __forceinline__ void append_candidates(Enum& en, uint64_t* top, int t
     __syncthreads();
 }
 
-// The entries of a window's table, enumerated through its entry list
-// (thread t takes entries t, t + T, ...).
-template <int T>
+constexpr int HEMPTY = -1;
+
+// The entries of a window's table (thread t takes slots t, t + T, ...).
+template <int T, int HS>
 struct TableEnum {
     const int* hkey;
     const float* hval;
-    const uint16_t* elist;
-    int nent;
     __device__ int count(uint64_t tau) const {
         int c = 0;
-        for (int e = threadIdx.x; e < nent; e += T) {
-            const int h = elist[e];
-            c += make_key(hval[h], hkey[h]) > tau;
+        for (int h = threadIdx.x; h < HS; h += T) {
+            const int row = hkey[h];
+            if (row != HEMPTY) c += make_key(hval[h], row) > tau;
         }
         return c;
     }
     __device__ void emit(uint64_t tau, uint64_t* dst, int base) const {
-        for (int e = threadIdx.x; e < nent; e += T) {
-            const int h = elist[e];
-            const uint64_t k = make_key(hval[h], hkey[h]);
-            if (k > tau) dst[base++] = k;
+        for (int h = threadIdx.x; h < HS; h += T) {
+            const int row = hkey[h];
+            if (row != HEMPTY) {
+                const uint64_t k = make_key(hval[h], row);
+                if (k > tau) dst[base++] = k;
+            }
         }
     }
 };
 
-constexpr int HEMPTY = -1;
-
-// Add product v at row into the window's table; called by all 32 lanes
-// (valid marks the lanes that carry a product).  New keys are claimed by
-// compare-and-swap and their slots appended (warp-aggregated) to the entry
-// list; more than LIM entries, or a probe run over the whole table, marks
-// the window as overflowed (its products are then redone in halves).
-template <int HS, int LIM, int ELCAP>
-__device__ __forceinline__ void table_add(bool valid, int row, float v, int* hkey, float* hval,
-                                          uint16_t* elist, WinShared* sh) {
+// Add product v at row into the window's table: the row's slot is found by
+// linear probing from a multiplicative hash and claimed by compare-and-swap.
+// A probe run longer than PMAX slots marks the window as overflowed (its
+// products are then redone in halves); nothing is added in that case.
+template <int HS>
+__device__ __forceinline__ void table_add(int row, float v, int* hkey, float* hval, WinShared* sh) {
     constexpr int LOGHS = HS == 1024 ? 10 : HS == 2048 ? 11 : HS == 4096 ? 12 : HS == 8192 ? 13 : 0;
     static_assert(LOGHS > 0, "table size");
-    int h = 0;
-    bool isnew = false;
-    if (valid) {
-        h = (int)(((uint32_t)row * 0x9E3779B1u) >> (32 - LOGHS));
-        for (int probes = 0;; ++probes) {
-            const int k = *(volatile int*)(hkey + h);
-            if (k == row) break;
-            if (k == HEMPTY) {
-                const int old = atomicCAS(hkey + h, HEMPTY, row);
-                if (old == HEMPTY) {
-                    isnew = true;
-                    break;
-                }
-                if (old == row) break;
-            }
-            h = (h + 1) & (HS - 1);
-            if (probes >= HS) {
-                valid = false;
-                sh->ovf = 1;
-                break;
-            }
+    constexpr int PMAX = 64;
+    int h = (int)(((uint32_t)row * 0x9E3779B1u) >> (32 - LOGHS));
+    for (int probes = 0;; ++probes) {
+        const int old = atomicCAS(hkey + h, HEMPTY, row);
+        if (old == HEMPTY || old == row) {
+            atomicAdd(hval + h, v);
+            return;
         }
-        if (valid) atomicAdd(hval + h, v);
-    }
-    const unsigned nm = __ballot_sync(FULL, isnew);
-    if (nm) {
-        const int lane = threadIdx.x & 31;
-        const int leader = __ffs(nm) - 1;
-        int base = 0;
-        if (lane == leader) {
-            base = atomicAdd(&sh->nent, __popc(nm));
-            if (base + __popc(nm) > LIM) sh->ovf = 1;
+        if (probes >= PMAX) {
+            sh->ovf = 1;
+            return;
         }
-        base = __shfl_sync(FULL, base, leader);
-        if (isnew) {
-            const int e = base + __popc(nm & lanemask_lt());
-            if (e < ELCAP) elist[e] = (uint16_t)h;
-        }
+        h = (h + 1) & (HS - 1);
     }
 }
 
@@ -356,12 +328,10 @@ struct ExpandArgs {
     int conf;
 };
 
-template <int T, int HS, int LIM>
+template <int T, int HS, int PLAN>
 struct ExpandLayout {
-    static constexpr int ELCAP = LIM + 32;
     static constexpr size_t bytes(int ksel) {
-        return (size_t)HS * 8 + (size_t)(ksel + LIM) * 8 + 256 * 4 + 256 * 8 + sizeof(WinShared) +
-               (size_t)ELCAP * 2;
+        return (size_t)HS * 8 + (size_t)(ksel + HS) * 8 + 256 * 4 + 256 * 8 + sizeof(WinShared);
     }
 };
 
@@ -384,21 +354,19 @@ struct FastDiv {
     }
 };
 
-template <int T, int HS, int LIM, int MINB>
+template <int T, int HS, int PLAN, int MINB>
 __global__ void __launch_bounds__(T, MINB) k_expand(ExpandArgs a) {
     constexpr int IPT = 8;
-    constexpr int ELCAP = ExpandLayout<T, HS, LIM>::ELCAP;
-    constexpr int TGT = LIM * 3 / 4;  // planned entries per window
+    static_assert(HS % (4 * T) == 0, "table clears in int4 stores");
     extern __shared__ __align__(16) unsigned char smem[];
     int* hkey = reinterpret_cast<int*>(smem);
     float* hval = reinterpret_cast<float*>(hkey + HS);
     uint64_t* top = reinterpret_cast<uint64_t*>(hval + HS);
     const int ksel = a.pp.ksel;
-    const int topcap = ksel + LIM;
+    const int topcap = ksel + HS;  // a window adds at most HS candidates
     unsigned* hist = reinterpret_cast<unsigned*>(top + topcap);
     unsigned long long* mhist = reinterpret_cast<unsigned long long*>(hist + 256);
     WinShared* sh = reinterpret_cast<WinShared*>(mhist + 256);
-    uint16_t* elist = reinterpret_cast<uint16_t*>(sh + 1);
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const CscView& A = a.A;
@@ -458,8 +426,8 @@ __global__ void __launch_bounds__(T, MINB) k_expand(ExpandArgs a) {
             meta.akj[i] = akj;
             s_sum += (double)akj * b.colsum[k];
         }
-        // ---- plan: windows of equal row width holding ~TGT entries each ----
-        int64_t nw64 = (est + TGT - 1) / TGT;
+        // ---- plan: windows of equal row width holding ~PLAN entries each ----
+        int64_t nw64 = (est + PLAN - 1) / PLAN;
         if (nw64 < 1) nw64 = 1;
         if (nw64 > span) nw64 = span;
         bool bucket = false;
@@ -501,12 +469,18 @@ __global__ void __launch_bounds__(T, MINB) k_expand(ExpandArgs a) {
                     }
 #pragma unroll
                     for (int c = 0; c < 4; ++c) {
+                        // rows are sorted, so equal windows form runs of lanes
                         const bool v = pb + 32 * c + lane < len;
-                        const unsigned act = __ballot_sync(FULL, v);
-                        if (v) {
-                            const uint32_t w = fdiv.div((uint32_t)(rr[c] - lo));
-                            const unsigned grp = __match_any_sync(act, w);
-                            if (__ffs(grp) - 1 == lane) atomicAdd(wcnt + w, __popc(grp));
+                        const unsigned act = __ballot_sync(FULL, v);  // a prefix of the lanes
+                        if (act == 0u) break;
+                        const uint32_t w = v ? fdiv.div((uint32_t)(rr[c] - lo)) : 0xFFFFFFFFu;
+                        const uint32_t wp = __shfl_up_sync(FULL, w, 1);
+                        const bool head = v && (lane == 0 || wp != w);
+                        const unsigned heads = __ballot_sync(FULL, head);
+                        if (head) {
+                            const unsigned after = heads & ~((2u << lane) - 1u);
+                            const int end = after ? __ffs(after) - 1 : __popc(act);
+                            atomicAdd(wcnt + w, end - lane);
                         }
                     }
                 }
@@ -553,19 +527,26 @@ __global__ void __launch_bounds__(T, MINB) k_expand(ExpandArgs a) {
 #pragma unroll
                     for (int c = 0; c < 4; ++c) {
                         const bool v = pb + 32 * c + lane < len;
-                        const unsigned act = __ballot_sync(FULL, v);
+                        const unsigned act = __ballot_sync(FULL, v);  // a prefix of the lanes
+                        if (act == 0u) break;
+                        const int row = rr[c];
+                        const uint32_t w = v ? fdiv.div((uint32_t)(row - lo)) : 0xFFFFFFFFu;
+                        const uint32_t wp = __shfl_up_sync(FULL, w, 1);
+                        const bool head = v && (lane == 0 || wp != w);
+                        const unsigned heads = __ballot_sync(FULL, head);
+                        int base = 0;
+                        if (head) {
+                            const unsigned after = heads & ~((2u << lane) - 1u);
+                            const int end = after ? __ffs(after) - 1 : __popc(act);
+                            base = atomicAdd(wcur + w, end - lane);
+                        }
+                        // the head of this lane's run: the highest head at or below it
+                        const int hl = 31 - __clz(heads & ((2u << lane) - 1u));
+                        base = __shfl_sync(FULL, base, hl);
                         if (v) {
-                            const int row = rr[c];
-                            const float prod = pv[c] * akj;
-                            const uint32_t w = fdiv.div((uint32_t)(row - lo));
-                            const unsigned grp = __match_any_sync(act, w);
-                            const int leader = __ffs(grp) - 1;
-                            int base = 0;
-                            if (lane == leader) base = atomicAdd(wcur + w, __popc(grp));
-                            base = __shfl_sync(grp, base, leader);
-                            const int pos = base + __popc(grp & lanemask_lt());
+                            const int pos = base + lane - hl;
                             brow[pos] = row;
-                            bval[pos] = prod;
+                            bval[pos] = pv[c] * akj;
                         }
                     }
                 }
@@ -588,7 +569,6 @@ __global__ void __launch_bounds__(T, MINB) k_expand(ExpandArgs a) {
             !bucket && (double)flops_j * (double)width < (double)LANE_MODE_MAX * (double)d * (double)span;
         while (r0 < hiE) {
             if (tid == 0) {
-                sh->nent = 0;
                 sh->ovf = 0;
                 sh->next = 0;
             }
@@ -597,53 +577,37 @@ __global__ void __launch_bounds__(T, MINB) k_expand(ExpandArgs a) {
             if (bucket) {
                 const int bs = woff[win], be = woff[win + 1];
                 const bool filt = r0 != lo + win * width || r1 != wr1;
-                for (int pb = bs + warp * 32; pb < be; pb += T) {
-                    const int p = pb + lane;
-                    bool valid = p < be;
-                    int row = 0;
-                    float v = 0.0f;
-                    if (valid) {
-                        row = brow[p];
-                        v = bval[p];
-                        if (filt) valid = row >= r0 && row < r1;
+                // four products per lane in flight before the table updates
+                for (int pb = bs + warp * 128; pb < be; pb += T * 4) {
+                    int rr[4];
+                    float pv[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int p = pb + 32 * u + lane;
+                        rr[u] = p < be ? brow[p] : -1;
+                        pv[u] = p < be ? bval[p] : 0.0f;
                     }
-                    table_add<HS, LIM, ELCAP>(valid, row, v, hkey, hval, elist, sh);
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        bool valid = rr[u] >= 0;
+                        if (filt) valid = valid && rr[u] >= r0 && rr[u] < r1;
+                        if (valid) table_add<HS>(rr[u], pv[u], hkey, hval, sh);
+                    }
                 }
             } else if (lane_mode) {
-                for (int kb = warp * 32; kb < d; kb += T) {
-                    const int kidx = kb + lane;
-                    int len = 0, pos = 0;
-                    const int32_t* rows = nullptr;
-                    const float* vv = nullptr;
-                    float akj = 0.0f;
-                    bool more = kidx < d;
-                    if (more) {
-                        const int64_t ks = meta.ks[kidx];
-                        rows = A.rowidx + ks;
-                        vv = A.val + ks;
-                        len = meta.len[kidx];
-                        akj = meta.akj[kidx];
-                        pos = cur[kidx];
+                for (int kidx = tid; kidx < d; kidx += T) {
+                    const int64_t ks = meta.ks[kidx];
+                    const int32_t* rows = A.rowidx + ks;
+                    const float* vv = A.val + ks;
+                    const float akj = meta.akj[kidx];
+                    const int len = meta.len[kidx];
+                    int pos = cur[kidx];
+                    for (; pos < len; ++pos) {
+                        const int row = __ldg(rows + pos);
+                        if (row >= r1) break;
+                        table_add<HS>(row, __ldg(vv + pos) * akj, hkey, hval, sh);
                     }
-                    while (__any_sync(FULL, more)) {
-                        bool valid = false;
-                        int row = 0;
-                        float v = 0.0f;
-                        if (more) {
-                            if (pos < len) {
-                                row = __ldg(rows + pos);
-                                valid = row < r1;
-                            }
-                            if (valid) {
-                                v = __ldg(vv + pos) * akj;
-                                ++pos;
-                            } else {
-                                more = false;
-                            }
-                        }
-                        table_add<HS, LIM, ELCAP>(valid, row, v, hkey, hval, elist, sh);
-                    }
-                    if (kidx < d) nxt[kidx] = pos;
+                    nxt[kidx] = pos;
                 }
             } else {
                 for (;;) {
@@ -661,8 +625,7 @@ __global__ void __launch_bounds__(T, MINB) k_expand(ExpandArgs a) {
                         const int p = pos + lane;
                         const int row = p < len ? __ldg(rows + p) : INT_MAX;
                         const bool valid = row < r1;
-                        const float v = valid ? __ldg(vv + p) * akj : 0.0f;
-                        table_add<HS, LIM, ELCAP>(valid, row, v, hkey, hval, elist, sh);
+                        if (valid) table_add<HS>(row, __ldg(vv + p) * akj, hkey, hval, sh);
                         const int nin = __popc(__ballot_sync(FULL, valid));
                         pos += nin;
                         if (nin < 32) break;
@@ -671,12 +634,11 @@ __global__ void __launch_bounds__(T, MINB) k_expand(ExpandArgs a) {
                 }
             }
             __syncthreads();
-            const int nent = sh->nent;
-            if (sh->ovf || nent > LIM) {
+            if (sh->ovf) {
                 // halve the range and redo it (a single row never overflows)
-                for (int i = tid; i < HS; i += T) {
-                    hkey[i] = HEMPTY;
-                    hval[i] = 0.0f;
+                for (int i = tid * 4; i < HS; i += T * 4) {
+                    *reinterpret_cast<int4*>(hkey + i) = make_int4(HEMPTY, HEMPTY, HEMPTY, HEMPTY);
+                    *reinterpret_cast<float4*>(hval + i) = make_float4(0.f, 0.f, 0.f, 0.f);
                 }
                 if (tid == 0) atomicAdd(&ctr->splits, 1ull);
                 r1 = r0 + (r1 - r0) / 2;
@@ -684,26 +646,27 @@ __global__ void __launch_bounds__(T, MINB) k_expand(ExpandArgs a) {
                 continue;
             }
             // ---- 2. statistics and candidates ----
-            TableEnum<T> en{hkey, hval, elist, nent};
+            TableEnum<T, HS> en{hkey, hval};
             int c = 0;
-            float pmt = 0.0f;  // <= ceil(LIM / T) terms per thread and window
-            for (int e = tid; e < nent; e += T) {
-                const int h = elist[e];
-                const float v = hval[h];
-                if (v >= a.pp.theta) {
-                    ++s_t;
-                    pmt += v;
+            float pmt = 0.0f;  // HS / T terms per thread and window
+            for (int h = tid; h < HS; h += T) {
+                const int row = hkey[h];
+                if (row != HEMPTY) {
+                    const float v = hval[h];
+                    ++s_n;
+                    if (v >= a.pp.theta) {
+                        ++s_t;
+                        pmt += v;
+                    }
+                    c += make_key(v, row) > tau;
                 }
-                c += make_key(v, hkey[h]) > tau;
             }
-            if (tid == 0) s_n += nent;
             s_mt += (double)pmt;
             append_candidates<T, IPT>(en, top, topcap, ksel, ntop, tau, c, hist, sh);
-            // ---- 3. clear the used slots ----
-            for (int e = tid; e < nent; e += T) {
-                const int h = elist[e];
-                hkey[h] = HEMPTY;
-                hval[h] = 0.0f;
+            // ---- 3. clear the table ----
+            for (int i = tid * 4; i < HS; i += T * 4) {
+                *reinterpret_cast<int4*>(hkey + i) = make_int4(HEMPTY, HEMPTY, HEMPTY, HEMPTY);
+                *reinterpret_cast<float4*>(hval + i) = make_float4(0.f, 0.f, 0.f, 0.f);
             }
             if (!bucket) {  // cursors advance past the window
                 int32_t* t = cur;
@@ -741,13 +704,13 @@ __global__ void __launch_bounds__(T, MINB) k_expand(ExpandArgs a) {
 }
 
 // configurations: 0 = small columns, 1 = everything else (threads, table
-// slots, entries per window, CTAs per SM)
-#define CONF0 128, 1024, 512, 8
-#define CONF1 256, 2048, 1024, 4
+// slots, planned entries per window, CTAs per SM)
+#define CONF0 128, 1024, 384, 8
+#define CONF1 256, 2048, 768, 4
 
 size_t numeric_smem(int conf, int ksel) {
-    return conf == 0 ? ExpandLayout<128, 1024, 512>::bytes(ksel)
-                     : ExpandLayout<256, 2048, 1024>::bytes(ksel);
+    return conf == 0 ? ExpandLayout<128, 1024, 384>::bytes(ksel)
+                     : ExpandLayout<256, 2048, 768>::bytes(ksel);
 }
 
 int numeric_threads(int conf) { return conf == 0 ? 128 : 256; }
@@ -766,8 +729,8 @@ int numeric_grid(int conf, int ksel, int num_sms) {
     return occ * num_sms;
 }
 
-// distinct rows one window of each configuration holds (for binning)
-int conf_value_capacity(int conf) { return conf == 0 ? 512 : 1024; }
+// distinct rows one window of each configuration is planned for
+int conf_value_capacity(int conf) { return conf == 0 ? 384 : 768; }
 
 void launch_numeric(int conf, const CscView& A, const PruneParams& pp, const ExpandBuffers& b,
                     int grid, cudaStream_t s) {
