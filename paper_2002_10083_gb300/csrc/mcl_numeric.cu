@@ -4,7 +4,7 @@
 // One CTA owns one output column j at a time (persistent grid, LPT order).
 // The column's row span is cut into row windows sized from the output-size
 // estimate so that each holds about PLAN distinct rows (a table load near
-// 3/8):
+// 1/2):
 //
 //   1. insert:  every product a_ik * a_kj of the window is added into an
 //               open-addressing table (HS slots, row keys claimed by
@@ -121,15 +121,102 @@ struct SrcMeta {
     }
 };
 
+// Stable LSD radix sort of s[0..n) ascending by the field s[i] >> 32, whose
+// values are below 2^bits, eight bits per pass.  Warp w owns a contiguous
+// segment; per pass each warp counts its digits (whist[w][digit]), one block
+// scan over (digit, warp) turns the counts into start offsets, and each warp
+// scatters its segment in order (equal digits of a 32-element chunk are
+// ranked by lane), so the sort is stable.  tmp holds n elements; whist holds
+// (T / 32) * 256 counters.  Ends with a barrier.
+template <int T>
+__device__ void block_radix_sort_hi(uint64_t* s, uint64_t* tmp, int n, int bits, unsigned* whist,
+                                    int* wsm) {
+    constexpr int NW = T / 32;
+    constexpr int DPT = 256 / T;  // digits per thread in the offset scan
+    static_assert(256 % T == 0, "digits per thread");
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int seg = ((n + NW - 1) / NW + 31) & ~31;
+    const int w0 = min(n, warp * seg), w1 = min(n, w0 + seg);
+    uint64_t* src = s;
+    uint64_t* dst = tmp;
+    for (int sh = 0; sh < bits; sh += 8) {
+        for (int i = tid; i < NW * 256; i += T) whist[i] = 0u;
+        __syncthreads();
+        for (int base = w0; base < w1; base += 32) {
+            const int i = base + lane;
+            const bool v = i < w1;
+            const unsigned dg = v ? (unsigned)(src[i] >> (32 + sh)) & 255u : 0u;
+            const unsigned act = __ballot_sync(FULL, v);
+            if (v) {
+                const unsigned grp = __match_any_sync(act, dg);
+                if (__ffs(grp) - 1 == lane) whist[warp * 256 + dg] += (unsigned)__popc(grp);
+            }
+            __syncwarp();
+        }
+        __syncthreads();
+        {
+            unsigned c[DPT][NW];
+            int tot = 0;
+#pragma unroll
+            for (int q = 0; q < DPT; ++q)
+#pragma unroll
+                for (int w = 0; w < NW; ++w) {
+                    c[q][w] = whist[w * 256 + tid * DPT + q];
+                    tot += (int)c[q][w];
+                }
+            int total;
+            int run = block_scan_excl<T>(tot, &total, wsm);
+#pragma unroll
+            for (int q = 0; q < DPT; ++q)
+#pragma unroll
+                for (int w = 0; w < NW; ++w) {
+                    whist[w * 256 + tid * DPT + q] = (unsigned)run;
+                    run += (int)c[q][w];
+                }
+        }
+        __syncthreads();
+        for (int base = w0; base < w1; base += 32) {
+            const int i = base + lane;
+            const bool v = i < w1;
+            uint64_t x = 0;
+            unsigned dg = 0;
+            if (v) {
+                x = src[i];
+                dg = (unsigned)(x >> (32 + sh)) & 255u;
+            }
+            const unsigned act = __ballot_sync(FULL, v);
+            if (v) {
+                const unsigned grp = __match_any_sync(act, dg);
+                dst[whist[warp * 256 + dg] + __popc(grp & lanemask_lt())] = x;
+                __syncwarp(act);
+                if (__ffs(grp) - 1 == lane) whist[warp * 256 + dg] += (unsigned)__popc(grp);
+            }
+            __syncwarp();
+        }
+        __syncthreads();
+        uint64_t* t = src;
+        src = dst;
+        dst = t;
+    }
+    if (src != s) {
+        for (int i = tid; i < n; i += T) s[i] = src[i];
+        __syncthreads();
+    }
+}
+
 // Finish a column: prune rule on the candidate keys top[0..ntop) plus exact
 // statistics, then the kept keys in row order (sorted here unless the
 // buffer is already row-ordered) written with inflation (pp.inflate) or
 // their B values; returns m* and chaos_j via the pointers.
+// For an unordered buffer, rows lie in [row_lo, row_lo + row_span); the
+// radix sort uses top[m .. topcap) and rscratch ((T / 32) * 256 counters)
+// as scratch when they suffice, the bitonic network otherwise.
 template <int T, int IPT, bool ROW_ORDERED>
-__device__ void finish_column(uint64_t* top, int ntop, const PruneParams& pp, double S, double MT,
-                              long long Tt, int64_t cap, int32_t* out_row, float* out_val,
-                              unsigned* hist, unsigned long long* mhist, WinShared* sh, DevCounters* ctr,
-                              int* mstar_out, double* chaos_out) {
+__device__ void finish_column(uint64_t* top, int ntop, int topcap, const PruneParams& pp, double S,
+                              double MT, long long Tt, int64_t cap, int32_t* out_row,
+                              float* out_val, unsigned* hist, unsigned long long* mhist,
+                              WinShared* sh, DevCounters* ctr, int row_lo, int row_span,
+                              unsigned* rscratch, int* mstar_out, double* chaos_out) {
     const int tid = threadIdx.x;
     const double target = (double)pp.p * S;
     const int q = (int)(Tt < (long long)pp.K ? Tt : (long long)pp.K);
@@ -194,16 +281,21 @@ __device__ void finish_column(uint64_t* top, int ntop, const PruneParams& pp, do
         m = m < mstar ? m : mstar;
     }
     if (!ROW_ORDERED && m > 1) {
-        // re-key as (row, value bits) and sort ascending: rows are distinct
+        // re-key as (row - row_lo, value bits) and sort ascending: rows are distinct
         for (int i = tid; i < m; i += T) {
             const uint64_t x = top[i];
-            top[i] = ((uint64_t)(uint32_t)key_row(x) << 32) | (x >> 32);
+            top[i] = ((uint64_t)(uint32_t)(key_row(x) - row_lo) << 32) | (x >> 32);
         }
         __syncthreads();
-        block_sort_asc<T>(top, m);
+        if (rscratch != nullptr && topcap - m >= m) {
+            const int bits = 32 - __clz(row_span - 1);
+            block_radix_sort_hi<T>(top, top + m, m, bits, rscratch, sh->wsm);
+        } else {
+            block_sort_asc<T>(top, m);
+        }
         for (int i = tid; i < m; i += T) {
             const uint64_t x = top[i];
-            top[i] = make_key(__uint_as_float((uint32_t)x), (int)(x >> 32));
+            top[i] = make_key(__uint_as_float((uint32_t)x), (int)(x >> 32) + row_lo);
         }
         __syncthreads();
     }
@@ -298,12 +390,18 @@ struct TableEnum {
 // A probe run longer than PMAX slots marks the window as overflowed (its
 // products are then redone in halves); nothing is added in that case.
 template <int HS>
-__device__ __forceinline__ void table_add(int row, float v, int* hkey, float* hval, WinShared* sh) {
+__device__ __forceinline__ int table_home(int row) {
     constexpr int LOGHS = HS == 1024 ? 10 : HS == 2048 ? 11 : HS == 4096 ? 12 : HS == 8192 ? 13 : 0;
     static_assert(LOGHS > 0, "table size");
+    return (int)(((uint32_t)row * 0x9E3779B1u) >> (32 - LOGHS));
+}
+
+// Linear probing from slot h (probes already made: p0).
+template <int HS>
+__device__ __forceinline__ void table_add_from(int row, float v, int h, int p0, int* hkey,
+                                               float* hval, WinShared* sh) {
     constexpr int PMAX = 64;
-    int h = (int)(((uint32_t)row * 0x9E3779B1u) >> (32 - LOGHS));
-    for (int probes = 0;; ++probes) {
+    for (int probes = p0;; ++probes) {
         const int old = atomicCAS(hkey + h, HEMPTY, row);
         if (old == HEMPTY || old == row) {
             atomicAdd(hval + h, v);
@@ -315,6 +413,11 @@ __device__ __forceinline__ void table_add(int row, float v, int* hkey, float* hv
         }
         h = (h + 1) & (HS - 1);
     }
+}
+
+template <int HS>
+__device__ __forceinline__ void table_add(int row, float v, int* hkey, float* hval, WinShared* sh) {
+    table_add_from<HS>(row, v, table_home<HS>(row), 0, hkey, hval, sh);
 }
 
 // Expected entries per source and window below which a window walks its
@@ -358,6 +461,7 @@ template <int T, int HS, int PLAN, int MINB>
 __global__ void __launch_bounds__(T, MINB) k_expand(ExpandArgs a) {
     constexpr int IPT = 8;
     static_assert(HS % (4 * T) == 0, "table clears in int4 stores");
+    static_assert(HS >= (T / 32) * 256, "the row sort's counters fit in the table");
     extern __shared__ __align__(16) unsigned char smem[];
     int* hkey = reinterpret_cast<int*>(smem);
     float* hval = reinterpret_cast<float*>(hkey + HS);
@@ -690,10 +794,12 @@ __global__ void __launch_bounds__(T, MINB) k_expand(ExpandArgs a) {
         int mstar = 0;
         double ch = 0.0;
         const int64_t obase = b.off[j];
-        finish_column<T, IPT, false>(top, ntop, a.pp, dv[0], dv[1], qv[0], b.cap[j],
+        // the table's key array is free here: radix counters of the row sort
+        finish_column<T, IPT, false>(top, ntop, topcap, a.pp, dv[0], dv[1], qv[0], b.cap[j],
                                      b.tmp_row + (obase - b.tmp_off0),
-                                     b.tmp_val + (obase - b.tmp_off0), hist, mhist, sh, ctr,
-                                     &mstar, &ch);
+                                     b.tmp_val + (obase - b.tmp_off0), hist, mhist, sh, ctr, lo,
+                                     span, reinterpret_cast<unsigned*>(hkey), &mstar, &ch);
+        for (int i = tid; i < (T / 32) * 256; i += T) hkey[i] = HEMPTY;
         if (tid == 0) {
             b.kept[j] = mstar;
             b.chaos[j] = ch;
@@ -705,12 +811,12 @@ __global__ void __launch_bounds__(T, MINB) k_expand(ExpandArgs a) {
 
 // configurations: 0 = small columns, 1 = everything else (threads, table
 // slots, planned entries per window, CTAs per SM)
-#define CONF0 128, 1024, 384, 8
-#define CONF1 256, 2048, 768, 4
+#define CONF0 128, 1024, 512, 8
+#define CONF1 256, 2048, 1024, 4
 
 size_t numeric_smem(int conf, int ksel) {
-    return conf == 0 ? ExpandLayout<128, 1024, 384>::bytes(ksel)
-                     : ExpandLayout<256, 2048, 768>::bytes(ksel);
+    return conf == 0 ? ExpandLayout<128, 1024, 512>::bytes(ksel)
+                     : ExpandLayout<256, 2048, 1024>::bytes(ksel);
 }
 
 int numeric_threads(int conf) { return conf == 0 ? 128 : 256; }
@@ -730,7 +836,7 @@ int numeric_grid(int conf, int ksel, int num_sms) {
 }
 
 // distinct rows one window of each configuration is planned for
-int conf_value_capacity(int conf) { return conf == 0 ? 384 : 768; }
+int conf_value_capacity(int conf) { return conf == 0 ? 512 : 1024; }
 
 void launch_numeric(int conf, const CscView& A, const PruneParams& pp, const ExpandBuffers& b,
                     int grid, cudaStream_t s) {
@@ -819,10 +925,10 @@ __global__ void __launch_bounds__(PR_T) k_prune(PruneArgs2 a) {
         int mstar = 0;
         double ch = 0.0;
         const int64_t obase = b.off[j];
-        finish_column<PR_T, 8, true>(top, ntop, a.pp, dv[0], dv[1], qv[0], b.cap[j],
+        finish_column<PR_T, 8, true>(top, ntop, topcap, a.pp, dv[0], dv[1], qv[0], b.cap[j],
                                      b.tmp_row + (obase - b.tmp_off0),
-                                     b.tmp_val + (obase - b.tmp_off0), hist, mhist, sh, b.ctr,
-                                     &mstar, &ch);
+                                     b.tmp_val + (obase - b.tmp_off0), hist, mhist, sh, b.ctr, 0,
+                                     0, nullptr, &mstar, &ch);
         if (tid == 0) {
             b.kept[j] = mstar;
             b.chaos[j] = ch;
