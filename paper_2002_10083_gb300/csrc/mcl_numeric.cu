@@ -19,7 +19,8 @@
 // Windows come from per-window product buckets (a counting pass and a
 // scatter of (row, product) into window order) or, without bucket space,
 // from per-source cursors over the sorted rows.  A window whose probe runs
-// exceed PMAX slots is halved and redone (counted as a split); results never
+// exceed PMAX slots is split by rows and redone (counted as a split), and
+// the rest of the column starts at the width that fitted; results never
 // depend on the size estimate.  Finally the prune rule picks m* (threshold /
 // top-k / recovery), the kept keys are sorted by row, inflated, renormalised
 // with an FP64 sum and written with chaos_j.
@@ -39,8 +40,12 @@ struct WinShared {
     int wsm[34];
     int item;
     int next;
-    int pad;
-    int ovf;  // the window exceeded its table
+    // window plan published by thread 0 (rows [pr0, pr1) when prs)
+    int pf0, pf1, pr0, pr1, prs, pdone;
+    // per-window flags, double-buffered by window parity
+    int ovf2[2];   // the window exceeded its table
+    int went2[2];  // entries of the window's table
+    int next2[2];  // source counter of the warp-per-source insert
 };
 
 // Exclusive block scan of one int per thread; *total gets the sum.  Three
@@ -399,7 +404,7 @@ __device__ __forceinline__ int table_home(int row) {
 // Linear probing from slot h (probes already made: p0).
 template <int HS>
 __device__ __forceinline__ void table_add_from(int row, float v, int h, int p0, int* hkey,
-                                               float* hval, WinShared* sh) {
+                                               float* hval, int* ovf) {
     constexpr int PMAX = 64;
     for (int probes = p0;; ++probes) {
         const int old = atomicCAS(hkey + h, HEMPTY, row);
@@ -408,7 +413,7 @@ __device__ __forceinline__ void table_add_from(int row, float v, int h, int p0, 
             return;
         }
         if (probes >= PMAX) {
-            sh->ovf = 1;
+            *ovf = 1;
             return;
         }
         h = (h + 1) & (HS - 1);
@@ -416,8 +421,8 @@ __device__ __forceinline__ void table_add_from(int row, float v, int h, int p0, 
 }
 
 template <int HS>
-__device__ __forceinline__ void table_add(int row, float v, int* hkey, float* hval, WinShared* sh) {
-    table_add_from<HS>(row, v, table_home<HS>(row), 0, hkey, hval, sh);
+__device__ __forceinline__ void table_add(int row, float v, int* hkey, float* hval, int* ovf) {
+    table_add_from<HS>(row, v, table_home<HS>(row), 0, hkey, hval, ovf);
 }
 
 // Expected entries per source and window below which a window walks its
@@ -530,7 +535,11 @@ __global__ void __launch_bounds__(T, MINB) k_expand(ExpandArgs a) {
             meta.akj[i] = akj;
             s_sum += (double)akj * b.colsum[k];
         }
-        // ---- plan: windows of equal row width holding ~PLAN entries each ----
+        // ---- plan: about est / PLAN windows of equal row width.  With bucket
+        // space the products go to per-window buckets, and a window that
+        // overflows the table is split by rows (later windows of the column
+        // then start at the split width).  Otherwise the window width adapts
+        // to the entries seen. ----
         int64_t nw64 = (est + PLAN - 1) / PLAN;
         if (nw64 < 1) nw64 = 1;
         if (nw64 > span) nw64 = span;
@@ -540,7 +549,7 @@ __global__ void __launch_bounds__(T, MINB) k_expand(ExpandArgs a) {
             if (nw64 > wmax) nw64 = wmax;
             bucket = true;
         }
-        int width = (int)(((int64_t)span + nw64 - 1) / nw64);
+        const int width = (int)(((int64_t)span + nw64 - 1) / nw64);
         const int nwin = (int)(((int64_t)span + width - 1) / width);
         int ntop = 0;
         uint64_t tau = 0;
@@ -662,25 +671,67 @@ __global__ void __launch_bounds__(T, MINB) k_expand(ExpandArgs a) {
             }
         }
 
-        // ---- windows: [r0, r1) inside window `win` = [lo + win*width, wr1) ----
-        int win = 0;
-        int r0 = lo;
-        int wr1 = (int)min((int64_t)lo + width, (int64_t)hiE);
-        int r1 = wr1;
+        // ---- windows ----
+        // Thread 0 plans every window and publishes it; bucket mode: bucket
+        // window f0 = [f0, f1) (rows [r0, r1) of it while it is split);
+        // cursor mode: rows [r0, r1).
+        int f0 = 0, f1 = 0;
+        bool rowsplit = false;
+        int split_w = 0;  // > 0: rows per piece when windows are being split
+        int r0 = lo, r1 = lo;
+        int cwidth = width;  // cursor mode: current window width
         int32_t* cur = meta.cur;
         int32_t* nxt = meta.nxt;
         const bool lane_mode =
             !bucket && (double)flops_j * (double)width < (double)LANE_MODE_MAX * (double)d * (double)span;
-        while (r0 < hiE) {
-            if (tid == 0) {
-                sh->ovf = 0;
-                sh->next = 0;
+        auto plan = [&](int f) {  // thread 0 only
+            while (f < nwin && woff[f + 1] == woff[f]) ++f;  // empty windows
+            f0 = f;
+            f1 = f;
+            rowsplit = false;
+            if (f >= nwin) return;
+            if (split_w > 0) {
+                const int ws = lo + f * width;
+                const int we = (int)min((int64_t)ws + width, (int64_t)hiE);
+                if (split_w < we - ws) {
+                    rowsplit = true;
+                    f1 = f + 1;
+                    r0 = ws;
+                    r1 = ws + split_w;
+                    return;
+                }
+                split_w = 0;
             }
-            __syncthreads();
-            // ---- 1. insert the products of rows [r0, r1) ----
+            f1 = f + 1;
+        };
+        auto publish = [&](int nextpar) {  // thread 0 only
+            sh->pf0 = f0;
+            sh->pf1 = f1;
+            sh->pr0 = r0;
+            sh->pr1 = r1;
+            sh->prs = rowsplit ? 1 : 0;
+            sh->pdone = bucket ? f0 >= nwin : r0 >= hiE;
+            sh->ovf2[nextpar] = 0;
+            sh->went2[nextpar] = 0;
+            sh->next2[nextpar] = 0;
+        };
+        if (tid == 0) {
+            if (bucket)
+                plan(0);
+            else
+                r1 = (int)min((int64_t)lo + cwidth, (int64_t)hiE);
+            publish(0);
+        }
+        for (int it = 0;; ++it) {
+            const int par = it & 1;
+            __syncthreads();  // this window's plan and flags are published
+            if (sh->pdone) break;
+            const int F0 = sh->pf0, F1 = sh->pf1, R0 = sh->pr0, R1 = sh->pr1;
+            const bool RS = sh->prs != 0;
+            int* ovfp = &sh->ovf2[par];
+            // ---- 1. insert the products of the window ----
             if (bucket) {
-                const int bs = woff[win], be = woff[win + 1];
-                const bool filt = r0 != lo + win * width || r1 != wr1;
+                const int bs = woff[F0], be = woff[F1];
                 // four products per lane in flight before the table updates
                 for (int pb = bs + warp * 128; pb < be; pb += T * 4) {
                     int rr[4];
@@ -694,8 +745,8 @@ __global__ void __launch_bounds__(T, MINB) k_expand(ExpandArgs a) {
 #pragma unroll
                     for (int u = 0; u < 4; ++u) {
                         bool valid = rr[u] >= 0;
-                        if (filt) valid = valid && rr[u] >= r0 && rr[u] < r1;
-                        if (valid) table_add<HS>(rr[u], pv[u], hkey, hval, sh);
+                        if (RS) valid = valid && rr[u] >= R0 && rr[u] < R1;
+                        if (valid) table_add<HS>(rr[u], pv[u], hkey, hval, ovfp);
                     }
                 }
             } else if (lane_mode) {
@@ -708,15 +759,15 @@ __global__ void __launch_bounds__(T, MINB) k_expand(ExpandArgs a) {
                     int pos = cur[kidx];
                     for (; pos < len; ++pos) {
                         const int row = __ldg(rows + pos);
-                        if (row >= r1) break;
-                        table_add<HS>(row, __ldg(vv + pos) * akj, hkey, hval, sh);
+                        if (row >= R1) break;
+                        table_add<HS>(row, __ldg(vv + pos) * akj, hkey, hval, ovfp);
                     }
                     nxt[kidx] = pos;
                 }
             } else {
                 for (;;) {
                     int kidx = 0;
-                    if (lane == 0) kidx = atomicAdd(&sh->next, 1);
+                    if (lane == 0) kidx = atomicAdd(&sh->next2[par], 1);
                     kidx = __shfl_sync(FULL, kidx, 0);
                     if (kidx >= d) break;
                     const int64_t ks = meta.ks[kidx];
@@ -728,8 +779,8 @@ __global__ void __launch_bounds__(T, MINB) k_expand(ExpandArgs a) {
                     while (pos < len) {
                         const int p = pos + lane;
                         const int row = p < len ? __ldg(rows + p) : INT_MAX;
-                        const bool valid = row < r1;
-                        if (valid) table_add<HS>(row, __ldg(vv + p) * akj, hkey, hval, sh);
+                        const bool valid = row < R1;
+                        if (valid) table_add<HS>(row, __ldg(vv + p) * akj, hkey, hval, ovfp);
                         const int nin = __popc(__ballot_sync(FULL, valid));
                         pos += nin;
                         if (nin < 32) break;
@@ -738,26 +789,36 @@ __global__ void __launch_bounds__(T, MINB) k_expand(ExpandArgs a) {
                 }
             }
             __syncthreads();
-            if (sh->ovf) {
-                // halve the range and redo it (a single row never overflows)
+            if (*ovfp) {
                 for (int i = tid * 4; i < HS; i += T * 4) {
                     *reinterpret_cast<int4*>(hkey + i) = make_int4(HEMPTY, HEMPTY, HEMPTY, HEMPTY);
                     *reinterpret_cast<float4*>(hval + i) = make_float4(0.f, 0.f, 0.f, 0.f);
                 }
-                if (tid == 0) atomicAdd(&ctr->splits, 1ull);
-                r1 = r0 + (r1 - r0) / 2;
-                __syncthreads();
+                if (tid == 0) {
+                    atomicAdd(&ctr->splits, 1ull);
+                    if (bucket && !rowsplit) {
+                        // split the window's rows (a single row never overflows)
+                        rowsplit = true;
+                        r0 = lo + f0 * width;
+                        const int we = (int)min((int64_t)r0 + width, (int64_t)hiE);
+                        r1 = r0 + (we - r0) / 2;
+                    } else {
+                        r1 = r0 + (r1 - r0) / 2;
+                        cwidth = r1 - r0;
+                    }
+                    publish(par ^ 1);
+                }
                 continue;
             }
             // ---- 2. statistics and candidates ----
             TableEnum<T, HS> en{hkey, hval};
-            int c = 0;
+            int c = 0, cnt = 0;
             float pmt = 0.0f;  // HS / T terms per thread and window
             for (int h = tid; h < HS; h += T) {
                 const int row = hkey[h];
                 if (row != HEMPTY) {
                     const float v = hval[h];
-                    ++s_n;
+                    ++cnt;
                     if (v >= a.pp.theta) {
                         ++s_t;
                         pmt += v;
@@ -765,7 +826,12 @@ __global__ void __launch_bounds__(T, MINB) k_expand(ExpandArgs a) {
                     c += make_key(v, row) > tau;
                 }
             }
+            s_n += cnt;
             s_mt += (double)pmt;
+            {
+                const int wc = warp_sum(cnt);
+                if (lane == 0 && wc) atomicAdd(&sh->went2[par], wc);
+            }
             append_candidates<T, IPT>(en, top, topcap, ksel, ntop, tau, c, hist, sh);
             // ---- 3. clear the table ----
             for (int i = tid * 4; i < HS; i += T * 4) {
@@ -777,16 +843,35 @@ __global__ void __launch_bounds__(T, MINB) k_expand(ExpandArgs a) {
                 cur = nxt;
                 nxt = t;
             }
-            r0 = r1;
-            if (r0 >= wr1) {
-                ++win;
-                if (bucket)
-                    while (win < nwin && woff[win + 1] == woff[win]) ++win;  // empty windows
-                r0 = (int)min((int64_t)lo + (int64_t)win * width, (int64_t)hiE);
-                wr1 = (int)min((int64_t)r0 + width, (int64_t)hiE);
+            // ---- 4. next window ----
+            if (tid == 0) {
+                const int went = sh->went2[par];  // complete: append_candidates ends with a barrier
+                if (bucket) {
+                    if (rowsplit) {
+                        const int we =
+                            (int)min((int64_t)lo + (int64_t)(f0 + 1) * width, (int64_t)hiE);
+                        int wd = r1 - r0;
+                        if (went < PLAN / 2 && wd < width) wd *= 2;
+                        r0 = r1;
+                        if (r0 >= we) {
+                            split_w = wd;
+                            plan(f0 + 1);
+                        } else {
+                            r1 = min(we, r0 + wd);
+                        }
+                    } else {
+                        plan(f1);
+                    }
+                } else {
+                    r0 = r1;
+                    if (went < PLAN / 2 && cwidth < (1 << 29))
+                        cwidth *= 2;
+                    else if (went > PLAN + PLAN / 2 && cwidth > 1)
+                        cwidth /= 2;
+                    r1 = (int)min((int64_t)r0 + cwidth, (int64_t)hiE);
+                }
+                publish(par ^ 1);
             }
-            r1 = wr1;
-            __syncthreads();
         }
         double dv[2] = {s_sum, s_mt};
         long long qv[2] = {s_t, s_n};
