@@ -51,6 +51,24 @@ def _peaks():
         return 6800.0, "fallback"
 
 
+def _traffic(flops):
+    """DRAM bytes of one numeric-pass launch: the ncu capture recorded under
+    profiles/ (read + write bytes of a smaller graph of the same family),
+    scaled by multiply-adds; None when the kernel sources changed since."""
+    import hashlib
+    try:
+        with open(os.path.join(ROOT, "profiles", "k_expand_traffic.json")) as f:
+            d = json.load(f)
+        for path, sha in d["sources_sha256"].items():
+            with open(os.path.join(ROOT, path), "rb") as g:
+                if hashlib.sha256(g.read()).hexdigest() != sha:
+                    return None
+        per_mac = (d["dram_bytes_read"] + d["dram_bytes_write"]) / d["multiply_adds"]
+        return int(per_mac * flops)
+    except Exception:
+        return None
+
+
 class ClockSampler:
     """nvidia-smi clock / throttle sampling during the timed region."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -315,7 +333,7 @@ def run_gpu(args):
         "cohen": form_line(ms_c, t_num_c, st_c),
         "speedup_learned_vs_plain": round((ms_o / ms) if main_name == "learned" else (ms / ms_o), 4),
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                     "frac": round(achieved / peak, 4), "traffic": None,
+                     "frac": round(achieved / peak, 4), "traffic": _traffic(flops),
                      "kernel": "k_expand (numeric pass, both configurations, one step)",
                      "algorithmic_bytes": b_alg, "kernel_ms": round(t_num, 3),
                      "peak_kind": peak_kind},
