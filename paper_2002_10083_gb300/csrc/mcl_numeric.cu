@@ -225,9 +225,13 @@ __device__ void finish_column(uint64_t* top, int ntop, int topcap, const PrunePa
     const int tid = threadIdx.x;
     const double target = (double)pp.p * S;
     const int q = (int)(Tt < (long long)pp.K ? Tt : (long long)pp.K);
-    double mq;
+    double mq = 0.0;
     uint64_t kq = 0;
-    if (Tt <= pp.K) {
+    // q >= Krec: m* = min(Krec, max(q, m_rec)) = Krec whatever the recovery
+    // finds, so neither the top-q mass nor m_rec is needed
+    const bool krec_bound = q >= pp.Krec;
+    if (krec_bound) {
+    } else if (Tt <= pp.K) {
         mq = MT;
     } else {
         kq = block_select_count<T>(top, ntop, top, 0, pp.K, hist, &sh->bs);
@@ -244,7 +248,9 @@ __device__ void finish_column(uint64_t* top, int ntop, int topcap, const PrunePa
     int mstar;
     uint64_t cut;
     bool have_cut = false;
-    if (target <= 0.0 || mq >= target) {
+    if (krec_bound) {
+        mstar = pp.Krec;
+    } else if (target <= 0.0 || mq >= target) {
         mstar = q;
         if (mstar <= pp.Krec) {
             if (Tt <= pp.K) {
@@ -364,36 +370,45 @@ __device__ __forceinline__ void append_candidates(Enum& en, uint64_t* top, int t
     __syncthreads();
 }
 
-constexpr int HEMPTY = -1;
+// Table slot: (bits(value) << 32) | row; empty = row -1, value +0.
+constexpr unsigned long long SLOT_EMPTY = 0x00000000FFFFFFFFull;
+
+__device__ __forceinline__ int slot_row(uint64_t x) { return (int)(uint32_t)x; }
+__device__ __forceinline__ float slot_val(uint64_t x) { return __uint_as_float((uint32_t)(x >> 32)); }
+// ranking key (value descending, row ascending) of an occupied slot
+__device__ __forceinline__ uint64_t slot_key(uint64_t x) {
+    return (x & 0xFFFFFFFF00000000ull) | (uint32_t)(0x7FFFFFFF - slot_row(x));
+}
 
 // The entries of a window's table (thread t takes slots t, t + T, ...).
 template <int T, int HS>
 struct TableEnum {
-    const int* hkey;
-    const float* hval;
+    const uint64_t* tab;
     __device__ int count(uint64_t tau) const {
         int c = 0;
         for (int h = threadIdx.x; h < HS; h += T) {
-            const int row = hkey[h];
-            if (row != HEMPTY) c += make_key(hval[h], row) > tau;
+            const uint64_t x = tab[h];
+            if (x != SLOT_EMPTY) c += slot_key(x) > tau;
         }
         return c;
     }
     __device__ void emit(uint64_t tau, uint64_t* dst, int base) const {
         for (int h = threadIdx.x; h < HS; h += T) {
-            const int row = hkey[h];
-            if (row != HEMPTY) {
-                const uint64_t k = make_key(hval[h], row);
+            const uint64_t x = tab[h];
+            if (x != SLOT_EMPTY) {
+                const uint64_t k = slot_key(x);
                 if (k > tau) dst[base++] = k;
             }
         }
     }
 };
 
-// Add product v at row into the window's table: the row's slot is found by
-// linear probing from a multiplicative hash and claimed by compare-and-swap.
-// A probe run longer than PMAX slots marks the window as overflowed (its
-// products are then redone in halves); nothing is added in that case.
+// Add product v at row into the window's table: linear probing from a
+// multiplicative hash; an empty slot is claimed with one 64-bit
+// compare-and-swap that stores the row and the first value together, and a
+// slot that already holds the row gets v added to its value half.  A probe
+// run longer than PMAX slots marks the window as overflowed (its products
+// are then redone in halves); nothing is added in that case.
 template <int HS>
 __device__ __forceinline__ int table_home(int row) {
     constexpr int LOGHS = HS == 1024 ? 10 : HS == 2048 ? 11 : HS == 4096 ? 12 : HS == 8192 ? 13 : 0;
@@ -401,15 +416,18 @@ __device__ __forceinline__ int table_home(int row) {
     return (int)(((uint32_t)row * 0x9E3779B1u) >> (32 - LOGHS));
 }
 
-// Linear probing from slot h (probes already made: p0).
 template <int HS>
-__device__ __forceinline__ void table_add_from(int row, float v, int h, int p0, int* hkey,
-                                               float* hval, int* ovf) {
+__device__ __forceinline__ void table_add(int row, float v, uint64_t* tab, int* ovf) {
     constexpr int PMAX = 64;
-    for (int probes = p0;; ++probes) {
-        const int old = atomicCAS(hkey + h, HEMPTY, row);
-        if (old == HEMPTY || old == row) {
-            atomicAdd(hval + h, v);
+    int h = table_home<HS>(row);
+    const unsigned long long mine =
+        ((unsigned long long)__float_as_uint(v) << 32) | (unsigned long long)(uint32_t)row;
+    for (int probes = 0;; ++probes) {
+        const unsigned long long old =
+            atomicCAS(reinterpret_cast<unsigned long long*>(tab + h), SLOT_EMPTY, mine);
+        if (old == SLOT_EMPTY) return;
+        if (slot_row(old) == row) {
+            atomicAdd(reinterpret_cast<float*>(tab + h) + 1, v);
             return;
         }
         if (probes >= PMAX) {
@@ -418,11 +436,6 @@ __device__ __forceinline__ void table_add_from(int row, float v, int h, int p0, 
         }
         h = (h + 1) & (HS - 1);
     }
-}
-
-template <int HS>
-__device__ __forceinline__ void table_add(int row, float v, int* hkey, float* hval, int* ovf) {
-    table_add_from<HS>(row, v, table_home<HS>(row), 0, hkey, hval, ovf);
 }
 
 // Expected entries per source and window below which a window walks its
@@ -465,12 +478,10 @@ struct FastDiv {
 template <int T, int HS, int PLAN, int MINB>
 __global__ void __launch_bounds__(T, MINB) k_expand(ExpandArgs a) {
     constexpr int IPT = 8;
-    static_assert(HS % (4 * T) == 0, "table clears in int4 stores");
-    static_assert(HS >= (T / 32) * 256, "the row sort's counters fit in the table");
+    static_assert(HS >= (T / 32) * 128, "the row sort's counters fit in the table");
     extern __shared__ __align__(16) unsigned char smem[];
-    int* hkey = reinterpret_cast<int*>(smem);
-    float* hval = reinterpret_cast<float*>(hkey + HS);
-    uint64_t* top = reinterpret_cast<uint64_t*>(hval + HS);
+    uint64_t* tab = reinterpret_cast<uint64_t*>(smem);
+    uint64_t* top = tab + HS;
     const int ksel = a.pp.ksel;
     const int topcap = ksel + HS;  // a window adds at most HS candidates
     unsigned* hist = reinterpret_cast<unsigned*>(top + topcap);
@@ -487,10 +498,7 @@ __global__ void __launch_bounds__(T, MINB) k_expand(ExpandArgs a) {
     int32_t* woff = b.woff ? b.woff + (int64_t)blockIdx.x * (WINDOW_MAX + 1) : nullptr;
     const int wbeg = ctr->bin_off[a.conf * NZ], wend = ctr->bin_off[a.conf * NZ + NZ];
 
-    for (int i = tid; i < HS; i += T) {
-        hkey[i] = HEMPTY;
-        hval[i] = 0.0f;
-    }
+    for (int i = tid; i < HS; i += T) tab[i] = SLOT_EMPTY;
     for (;;) {
         if (tid == 0) sh->item = atomicAdd(&ctr->conf_ctr[a.conf], 1);
         __syncthreads();
@@ -561,8 +569,8 @@ __global__ void __launch_bounds__(T, MINB) k_expand(ExpandArgs a) {
 
         if (bucket) {
             // ---- count the products of every window (counters in the table's key array) ----
-            int* wcnt = hkey;
-            int* wcur = reinterpret_cast<int*>(hval);
+            int* wcnt = reinterpret_cast<int*>(tab);  // nwin <= HS counters each
+            int* wcur = wcnt + HS;
             for (int i = tid; i < nwin; i += T) wcnt[i] = 0;
             if (tid == 0) sh->next = 0;
             __syncthreads();
@@ -665,10 +673,7 @@ __global__ void __launch_bounds__(T, MINB) k_expand(ExpandArgs a) {
                 }
             }
             __syncthreads();
-            for (int i = tid; i < nwin; i += T) {
-                hkey[i] = HEMPTY;
-                hval[i] = 0.0f;
-            }
+            for (int i = tid; i < HS; i += T) tab[i] = SLOT_EMPTY;
         }
 
         // ---- windows ----
@@ -746,7 +751,7 @@ __global__ void __launch_bounds__(T, MINB) k_expand(ExpandArgs a) {
                     for (int u = 0; u < 4; ++u) {
                         bool valid = rr[u] >= 0;
                         if (RS) valid = valid && rr[u] >= R0 && rr[u] < R1;
-                        if (valid) table_add<HS>(rr[u], pv[u], hkey, hval, ovfp);
+                        if (valid) table_add<HS>(rr[u], pv[u], tab, ovfp);
                     }
                 }
             } else if (lane_mode) {
@@ -760,7 +765,7 @@ __global__ void __launch_bounds__(T, MINB) k_expand(ExpandArgs a) {
                     for (; pos < len; ++pos) {
                         const int row = __ldg(rows + pos);
                         if (row >= R1) break;
-                        table_add<HS>(row, __ldg(vv + pos) * akj, hkey, hval, ovfp);
+                        table_add<HS>(row, __ldg(vv + pos) * akj, tab, ovfp);
                     }
                     nxt[kidx] = pos;
                 }
@@ -780,7 +785,7 @@ __global__ void __launch_bounds__(T, MINB) k_expand(ExpandArgs a) {
                         const int p = pos + lane;
                         const int row = p < len ? __ldg(rows + p) : INT_MAX;
                         const bool valid = row < R1;
-                        if (valid) table_add<HS>(row, __ldg(vv + p) * akj, hkey, hval, ovfp);
+                        if (valid) table_add<HS>(row, __ldg(vv + p) * akj, tab, ovfp);
                         const int nin = __popc(__ballot_sync(FULL, valid));
                         pos += nin;
                         if (nin < 32) break;
@@ -790,10 +795,7 @@ __global__ void __launch_bounds__(T, MINB) k_expand(ExpandArgs a) {
             }
             __syncthreads();
             if (*ovfp) {
-                for (int i = tid * 4; i < HS; i += T * 4) {
-                    *reinterpret_cast<int4*>(hkey + i) = make_int4(HEMPTY, HEMPTY, HEMPTY, HEMPTY);
-                    *reinterpret_cast<float4*>(hval + i) = make_float4(0.f, 0.f, 0.f, 0.f);
-                }
+                for (int i = tid; i < HS; i += T) tab[i] = SLOT_EMPTY;
                 if (tid == 0) {
                     atomicAdd(&ctr->splits, 1ull);
                     if (bucket && !rowsplit) {
@@ -811,19 +813,19 @@ __global__ void __launch_bounds__(T, MINB) k_expand(ExpandArgs a) {
                 continue;
             }
             // ---- 2. statistics and candidates ----
-            TableEnum<T, HS> en{hkey, hval};
+            TableEnum<T, HS> en{tab};
             int c = 0, cnt = 0;
             float pmt = 0.0f;  // HS / T terms per thread and window
             for (int h = tid; h < HS; h += T) {
-                const int row = hkey[h];
-                if (row != HEMPTY) {
-                    const float v = hval[h];
+                const uint64_t x = tab[h];
+                if (x != SLOT_EMPTY) {
+                    const float v = slot_val(x);
                     ++cnt;
                     if (v >= a.pp.theta) {
                         ++s_t;
                         pmt += v;
                     }
-                    c += make_key(v, row) > tau;
+                    c += slot_key(x) > tau;
                 }
             }
             s_n += cnt;
@@ -834,10 +836,7 @@ __global__ void __launch_bounds__(T, MINB) k_expand(ExpandArgs a) {
             }
             append_candidates<T, IPT>(en, top, topcap, ksel, ntop, tau, c, hist, sh);
             // ---- 3. clear the table ----
-            for (int i = tid * 4; i < HS; i += T * 4) {
-                *reinterpret_cast<int4*>(hkey + i) = make_int4(HEMPTY, HEMPTY, HEMPTY, HEMPTY);
-                *reinterpret_cast<float4*>(hval + i) = make_float4(0.f, 0.f, 0.f, 0.f);
-            }
+            for (int i = tid; i < HS; i += T) tab[i] = SLOT_EMPTY;
             if (!bucket) {  // cursors advance past the window
                 int32_t* t = cur;
                 cur = nxt;
@@ -883,8 +882,8 @@ __global__ void __launch_bounds__(T, MINB) k_expand(ExpandArgs a) {
         finish_column<T, IPT, false>(top, ntop, topcap, a.pp, dv[0], dv[1], qv[0], b.cap[j],
                                      b.tmp_row + (obase - b.tmp_off0),
                                      b.tmp_val + (obase - b.tmp_off0), hist, mhist, sh, ctr, lo,
-                                     span, reinterpret_cast<unsigned*>(hkey), &mstar, &ch);
-        for (int i = tid; i < (T / 32) * 256; i += T) hkey[i] = HEMPTY;
+                                     span, reinterpret_cast<unsigned*>(tab), &mstar, &ch);
+        for (int i = tid; i < (T / 32) * 128; i += T) tab[i] = SLOT_EMPTY;
         if (tid == 0) {
             b.kept[j] = mstar;
             b.chaos[j] = ch;
