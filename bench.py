@@ -223,6 +223,10 @@ def run_gpu(args):
     D = mcl.DeviceCSC.from_host(A, device=f"cuda:{dev}")
     ctx = mcl.Context(dev)
     meta = estimator.install(ctx)
+    # numeric-pass settings the autotuner stored for this device and workload class
+    from paper_2002_10083_gb300 import autotune
+    tuned = autotune.apply(ctx, autotune.load(), torch.cuda.get_device_name(dev),
+                           autotune.class_of_host(A))
     prm_plain = mcl.Params(**PARAMS)
     prm_learn = mcl.Params(**PARAMS, use_estimator=1)
     prm_main = prm_plain if args.form == "plain" else prm_learn
@@ -326,6 +330,7 @@ def run_gpu(args):
                                             "1-20", meta.get("eval", {}).get("median_abs_log_ratio", -1))
                                         if main_name == "learned" else " (exact symbolic sizing)"),
                    "l2": "inputs larger than L2 (A is %.0f MB)" % (in_bytes / 1e6),
+                   "tuning": tuned if tuned is not None else "library defaults",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "iters_per_s": round(world * 1000.0 / ms, 3),
         main_name: form_line(ms, t_num, st),
@@ -377,16 +382,22 @@ def run_batched(args):
     if args.phase_budget_gb:
         ctx.set_option(mcl.OPT_PHASE_BUDGET, int(args.phase_budget_gb * (1 << 30)))
     torch.cuda.synchronize()
-    # per-iteration flops are measured by running the iterations one by one
-    # with the same per-component retirement as mcl_run
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record()
-    lab, iters, hist, final, notconv = ctx.run(D, prm, comp_offsets=offs, keep_final=False)
-    e1.record()
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1)
-    st = ctx.stats()
+
+    def timed_run(graph: int):
+        ctx.set_option(mcl.OPT_GRAPH, graph)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        out = ctx.run(D, prm, comp_offsets=offs, keep_final=False)
+        e1.record()
+        torch.cuda.synchronize()
+        return out, e0.elapsed_time(e1), ctx.stats()
+
+    # eager loop (host decisions between the launches of an iteration), then
+    # the same run with iterations after the first replayed as CUDA graphs
+    (lab_e, iters_e, hist_e, _, nc_e), ms_e, st_e = timed_run(0)
+    (lab, iters, hist, final, notconv), ms, st = timed_run(1)
+    same = bool(torch.equal(lab, lab_e)) and iters == iters_e
     line = {"metric": METRIC, "workload": args.workload, "n": A.n, "nnz": A.nnz,
             "components": None if offs is None else len(offs) - 1,
             "iterations": iters, "converged": not notconv, "ms_total": round(ms, 1),
@@ -396,7 +407,11 @@ def run_batched(args):
             "last_iteration": {k: st[k] for k in ("flops", "nnz_b", "nnz_out", "phases",
                                                   "estimator_misses")},
             "generation_s": round(gen_s, 1), "form": "learned" if prm.use_estimator else "plain",
-            "phase_budget_gb": args.phase_budget_gb}
+            "phase_budget_gb": args.phase_budget_gb,
+            "graph_replays": int(st["graph_replays"]),
+            "eager": {"ms_total": round(ms_e, 1), "iters_per_s": round(iters_e / (ms_e / 1000.0), 4),
+                      "iterations": iters_e},
+            "graph_equals_eager": same}
     print(json.dumps(line), flush=True)
     return 0
 

@@ -107,6 +107,7 @@ typedef struct {
     int32_t bins_used;
     int32_t iterations;
     int32_t phases;           /* column batches of the last mcl_expand */
+    int32_t graph_replays;    /* iterations of the last batched mcl_run replayed as CUDA graphs */
 } mcl_stats;
 
 /* Create a context on `device` (made current by every call).  alloc/free
@@ -219,6 +220,14 @@ mcl_status mcl_symbolic(mcl_ctx* ctx, const mcl_csc* A, int64_t* flops, int64_t*
  *                        phased expansion of Section II, one GPU); 0 = off
  *   7 MCL_OPT_COHEN_KEYS keys per vertex of Cohen's estimate (2..16, default 8)
  *   8 MCL_OPT_COHEN_SEED seed of Cohen's keys (default 2002)
+ *   9 MCL_OPT_GRAPH      1 (default): a batched mcl_run (comp_offsets given,
+ *                        prm->batched, exact or flops-bound sizing) replays
+ *                        every iteration after the first as one CUDA graph
+ *                        (one host synchronisation per iteration); 0: eager
+ *  10 MCL_OPT_GRAPH_CAP  entries of each graph replay buffer; 0 (default):
+ *                        sum over components of size * min(size, K_rec), an
+ *                        upper bound on any later iteration.  An iteration
+ *                        that would exceed it is redone without graphs.
  * Returns MCL_ERR_INVALID for an unknown option or value.
  */
 #define MCL_OPT_SIZING 1
@@ -229,6 +238,8 @@ mcl_status mcl_symbolic(mcl_ctx* ctx, const mcl_csc* A, int64_t* flops, int64_t*
 #define MCL_OPT_PHASE_BUDGET 6
 #define MCL_OPT_COHEN_KEYS 7
 #define MCL_OPT_COHEN_SEED 8
+#define MCL_OPT_GRAPH 9
+#define MCL_OPT_GRAPH_CAP 10
 mcl_status mcl_set_option(mcl_ctx* ctx, int option, int64_t value);
 
 /*

@@ -43,6 +43,11 @@ struct mcl_ctx {
     int conf_mask = 0x3;    // numeric configurations allowed
     int validate = 1;
     int est_milli = 1000;   // estimate scale (test knob)
+    int graph_mode = 1;     // batched mcl_run replays iterations >= 2 as CUDA graphs
+    int small_max = 512;    // autotuned: small-configuration bound on the estimate
+    int table = 0;          // autotuned: shape of the large configuration
+    int plan = 0;           // autotuned: rows planned per window (0: half the table)
+    int64_t graph_cap = 0;  // entries of the replay buffers (0: per-component bound)
     // learned estimator (weights on device)
     Buf mlp_w, mlp_norm, colmax, feats, prev_logcf;
     int has_estimator = 0;
@@ -132,6 +137,9 @@ mcl_status check_params(mcl_ctx* c, const mcl_params* prm, PruneParams* pp, bool
         return fail(c, MCL_ERR_INVALID, "threshold must be finite and >= 0");
     if (need_inflation && !(prm->inflation > 0.0f && prm->inflation <= 1.0e6f))
         return fail(c, MCL_ERR_INVALID, "inflation must be > 0");
+    pp->small_max = c->small_max;
+    pp->table = c->table;
+    pp->plan = c->plan;
     pp->theta = prm->threshold;
     pp->K = prm->select_k;
     pp->p = prm->recover_pct;
@@ -177,6 +185,7 @@ ExpandBuffers buffers(mcl_ctx* c) {
     b.scan_tmp = (int64_t*)c->scan.p;
     b.ctr = (DevCounters*)c->ctr.p;
     b.active = nullptr;
+    b.nnz_is_bound = 0;
     b.bucket_row = nullptr;
     b.bucket_val = nullptr;
     b.woff = nullptr;
@@ -211,10 +220,10 @@ double chaos_from_bits(unsigned long long b) {
     return d;
 }
 
-int max_numeric_grid(mcl_ctx* c, int ksel) {
+int max_numeric_grid(mcl_ctx* c, const PruneParams& pp) {
     int g = 0;
     for (int q = 0; q < NCONF; ++q) {
-        int gq = numeric_grid(q, ksel, c->num_sms);
+        int gq = numeric_grid(q, pp, c->num_sms);
         if (gq > g) g = gq;
     }
     int gs = symbolic_grid(c->num_sms);
@@ -319,6 +328,25 @@ mcl_status mcl_set_option(mcl_ctx* c, int option, int64_t value) {
             if (value < 2 || value > cohen_max_r()) return fail(c, MCL_ERR_INVALID, "bad key count");
             c->cohen_r = (int)value;
             return MCL_OK;
+        case 9:  // graph replay of batched iterations (0 off, 1 on)
+            c->graph_mode = value != 0;
+            return MCL_OK;
+        case 10:  // entries of the graph replay buffers (0: per-component bound)
+            if (value < 0) return fail(c, MCL_ERR_INVALID, "bad capacity");
+            c->graph_cap = value;
+            return MCL_OK;
+        case 11:  // largest estimate of the small configuration
+            if (value < 0 || value > 512) return fail(c, MCL_ERR_INVALID, "small bound in [0, 512]");
+            c->small_max = (int)value;
+            return MCL_OK;
+        case 12:  // shape of the large configuration
+            if (value < 0 || value > 2) return fail(c, MCL_ERR_INVALID, "table shape in [0, 2]");
+            c->table = (int)value;
+            return MCL_OK;
+        case 13:  // rows planned per window of the large configuration (0: half the table)
+            if (value < 0 || value > 3072) return fail(c, MCL_ERR_INVALID, "plan in [0, 3072]");
+            c->plan = (int)value;
+            return MCL_OK;
         case 8:  // seed of Cohen's keys
             c->cohen_seed = (uint64_t)value;
             return MCL_OK;
@@ -360,7 +388,7 @@ static mcl_status expand_impl(mcl_ctx* c, const mcl_csc* A, const mcl_params* pr
     const int max_deg = c->hctr->max_deg;
     b.cur_stride = (max_deg + 31) & ~31;
     if (b.cur_stride < 32) b.cur_stride = 32;
-    const int grid_max = max_numeric_grid(c, pp.ksel);
+    const int grid_max = max_numeric_grid(c, pp);
     if (!ensure(c, c->cursors, (size_t)grid_max * 6 * b.cur_stride * 4, s))
         return fail(c, MCL_ERR_OOM, "cursor scratch allocation failed");
     b.cursors = (int32_t*)c->cursors.p;
@@ -406,7 +434,7 @@ static mcl_status expand_impl(mcl_ctx* c, const mcl_csc* A, const mcl_params* pr
         launch_binning(Av, pp, bb, c->conf_mask, s);
         for (int q = NCONF - 1; q >= 0; --q) {
             if (!((c->conf_mask >> q) & 1)) continue;
-            const int g = numeric_grid(q, pp.ksel, c->num_sms);
+            const int g = numeric_grid(q, pp, c->num_sms);
             ExpandBuffers bq = bb;
             bq.bucket_row = nullptr;
             bq.bucket_val = nullptr;
@@ -848,6 +876,161 @@ static void free_csc(mcl_ctx* c, mcl_csc* M, cudaStream_t s) {
     M->val = nullptr;
 }
 
+// ---------------------------------------------------------------------------
+// Batched iterations replayed as CUDA graphs.  After the first iteration
+// every column of an active component holds at most K_rec entries, so one
+// iteration needs no host decision: the replay buffers (two CSC matrices
+// and the output staging, each of `cap` entries) are allocated once and the
+// iteration X -> Y and its mirror Y -> X are captured.  One replay is every
+// kernel of an iteration plus a copy of the device counters to the host,
+// the only synchronisation.  If an iteration's output capacities exceed the
+// buffers, a device guard makes the numeric pass and the compaction write
+// nothing (ERR_STAGING) and the host redoes the iteration without graphs.
+// ---------------------------------------------------------------------------
+struct GraphRun {
+    cudaStream_t gs = nullptr;
+    cudaGraph_t g[2] = {nullptr, nullptr};
+    cudaGraphExec_t x[2] = {nullptr, nullptr};
+    mcl_csc buf[2] = {};
+    int64_t cap = 0;
+    int64_t kernels = 0;  // kernel nodes per replay
+};
+
+static void graph_release(mcl_ctx* c, GraphRun& G, cudaStream_t s, int keep) {
+    for (int q = 0; q < 2; ++q) {
+        if (G.x[q]) cudaGraphExecDestroy(G.x[q]);
+        if (G.g[q]) cudaGraphDestroy(G.g[q]);
+        G.x[q] = nullptr;
+        G.g[q] = nullptr;
+        if (q != keep) free_csc(c, &G.buf[q], s);
+    }
+    if (G.gs) {
+        cudaStreamSynchronize(G.gs);
+        cudaStreamDestroy(G.gs);
+        G.gs = nullptr;
+    }
+}
+
+// One batched iteration in -> out on stream s: kernel launches and memsets
+// only (capturable).  in.nnz is read as a capacity bound.
+static void static_iteration(mcl_ctx* c, const mcl_params* prm, const PruneParams& pp, int ncomp,
+                             const mcl_csc& in, const mcl_csc& out, int64_t cap, int sizing,
+                             int64_t stride, cudaStream_t s) {
+    const int32_t n = in.n;
+    ExpandBuffers b = buffers(c);
+    b.active = (const uint8_t*)c->active.p;
+    b.nnz_is_bound = 1;
+    b.cur_stride = stride;
+    b.tmp_off0 = 0;
+    const CscView Av{n, in.nnz, in.colptr, in.rowidx, in.val};
+    cudaMemsetAsync(c->ctr.p, 0, sizeof(DevCounters), s);
+    launch_active_from_comp(n, (const int32_t*)c->comp_of_col.p, (const uint8_t*)c->comp_active.p,
+                            (uint8_t*)c->active.p, s);
+    launch_colstats(Av, pp, b, c->num_sms, s);
+    const int grid_max = max_numeric_grid(c, pp);
+    if (sizing == 1) {
+        launch_est_from_flops(Av, b, s);
+    } else {
+        launch_symbolic(Av, b, b.est, c->num_sms, grid_max, s);
+        launch_cap_tighten(n, b.est, b.cap, b.active, s);
+    }
+    launch_exclusive_scan<int64_t>(b.cap, n, b.off, b.scan_tmp, &b.ctr->cap_total, s);
+    launch_staging_guard(b.ctr, cap, s);
+    launch_binning(Av, pp, b, c->conf_mask, s);
+    for (int q = NCONF - 1; q >= 0; --q) {
+        if (!((c->conf_mask >> q) & 1)) continue;
+        const int g = numeric_grid(q, pp, c->num_sms);
+        ExpandBuffers bq = b;
+        if (q == NCONF - 1 && c->bucket_row.p) {
+            bq.bucket_row = (int32_t*)c->bucket_row.p;
+            bq.bucket_val = (float*)c->bucket_val.p;
+            bq.woff = (int32_t*)c->woff.p;
+            bq.bucket_cap = (int64_t)(c->bucket_row.bytes / ((size_t)g * 4));
+        }
+        launch_numeric(q, Av, pp, bq, g, s);
+    }
+    launch_finalize_stats(n, b, s);
+    launch_fill_inactive(Av, b.active, b.kept, s);
+    launch_exclusive_scan<int32_t>(b.kept, n, out.colptr, b.scan_tmp, &b.ctr->nnz_out, s);
+    launch_compact(Av, b, out.colptr, out.rowidx, out.val, s);
+    cudaMemsetAsync(c->comp_bits.p, 0, (size_t)ncomp * 8, s);
+    launch_comp_chaos(n, (const int32_t*)c->comp_of_col.p, b.active, b.chaos,
+                      (unsigned long long*)c->comp_bits.p, s);
+    launch_comp_retire(ncomp, (const unsigned long long*)c->comp_bits.p, prm->chaos_eps,
+                       (uint8_t*)c->comp_active.p, b.ctr, s);
+    cudaMemcpyAsync(c->hctr, c->ctr.p, sizeof(DevCounters), cudaMemcpyDeviceToHost, s);
+}
+
+// Allocates the replay buffers, moves `cur` (the output of the first
+// iteration, owned) into the first one and captures both graphs.
+static mcl_status graph_prepare(mcl_ctx* c, const mcl_params* prm, const PruneParams& pp,
+                                const int32_t* comp_offsets, int ncomp, mcl_csc* cur, int sizing,
+                                GraphRun& G, cudaStream_t s) {
+    const int32_t n = cur->n;
+    int64_t cap = 0;  // entries of an iteration's output: column j keeps <= min(K_rec, |comp(j)|)
+    for (int q = 0; q < ncomp; ++q) {
+        const int64_t sz = comp_offsets[q + 1] - comp_offsets[q];
+        cap += sz * (sz < pp.Krec ? sz : pp.Krec);
+    }
+    if (c->graph_cap > 0 && c->graph_cap < cap) cap = c->graph_cap;
+    if (cap < cur->nnz) cap = cur->nnz;
+    if (cap < 1) cap = 1;
+    int64_t stride = ((int64_t)pp.Krec + 31) & ~31ll;
+    if (stride < 32) stride = 32;
+    const int grid_max = max_numeric_grid(c, pp);
+    const int g1 = numeric_grid(NCONF - 1, pp, c->num_sms);
+    int64_t capb = (int64_t)pp.Krec * pp.Krec;
+    const int64_t capb_max = (int64_t)(c->bucket_budget / ((size_t)g1 * 8));
+    if (capb > capb_max) capb = capb_max;
+    if (!ensure(c, c->tmp_row, (size_t)cap * 4 + 4, s) || !ensure(c, c->tmp_val, (size_t)cap * 4 + 4, s) ||
+        !ensure(c, c->cursors, (size_t)grid_max * 6 * stride * 4, s) ||
+        !ensure(c, c->comp_bits, (size_t)ncomp * 8, s))
+        return fail(c, MCL_ERR_OOM, "graph replay scratch allocation failed");
+    if (capb >= 1024 && ensure(c, c->bucket_row, (size_t)g1 * capb * 4, s) &&
+        ensure(c, c->bucket_val, (size_t)g1 * capb * 4, s) &&
+        ensure(c, c->woff, (size_t)g1 * (WINDOW_MAX + 1) * 4, s)) {
+        // exact per-CTA capacity recorded in the buffer sizes
+        c->bucket_row.bytes = (size_t)g1 * capb * 4;
+    } else {
+        dev_free(c, c->bucket_row.p, s);
+        c->bucket_row = Buf{};
+    }
+    for (int q = 0; q < 2; ++q) {
+        G.buf[q].n = n;
+        G.buf[q].nnz = cap;
+        G.buf[q].colptr = (int64_t*)dev_alloc(c, ((size_t)n + 1) * 8, s);
+        G.buf[q].rowidx = (int32_t*)dev_alloc(c, (size_t)cap * 4 + 4, s);
+        G.buf[q].val = (float*)dev_alloc(c, (size_t)cap * 4 + 4, s);
+        if (!G.buf[q].colptr || !G.buf[q].rowidx || !G.buf[q].val) {
+            for (int r = 0; r <= q; ++r) free_csc(c, &G.buf[r], s);
+            return fail(c, MCL_ERR_OOM, "graph replay buffers (%lld entries) do not fit", (long long)cap);
+        }
+    }
+    CUDA_TRY(c, cudaMemcpyAsync(G.buf[0].colptr, cur->colptr, ((size_t)n + 1) * 8,
+                                cudaMemcpyDeviceToDevice, s));
+    if (cur->nnz > 0) {
+        CUDA_TRY(c, cudaMemcpyAsync(G.buf[0].rowidx, cur->rowidx, (size_t)cur->nnz * 4,
+                                    cudaMemcpyDeviceToDevice, s));
+        CUDA_TRY(c, cudaMemcpyAsync(G.buf[0].val, cur->val, (size_t)cur->nnz * 4,
+                                    cudaMemcpyDeviceToDevice, s));
+    }
+    CUDA_TRY(c, cudaStreamSynchronize(s));
+    free_csc(c, cur, s);
+    CUDA_TRY(c, cudaStreamCreateWithFlags(&G.gs, cudaStreamNonBlocking));
+    G.cap = cap;
+    const long long l0 = launches_total();
+    for (int q = 0; q < 2; ++q) {
+        CUDA_TRY(c, cudaStreamBeginCapture(G.gs, cudaStreamCaptureModeRelaxed));
+        static_iteration(c, prm, pp, ncomp, G.buf[q], G.buf[q ^ 1], cap, sizing, stride, G.gs);
+        CUDA_TRY(c, cudaStreamEndCapture(G.gs, &G.g[q]));
+        CUDA_TRY(c, cudaGraphInstantiate(&G.x[q], G.g[q], 0));
+    }
+    const long long captured = launches_total() - l0;
+    count_launches((int)-captured);  // captured launches run at replay time
+    G.kernels = captured / 2;
+    return MCL_OK;
+}
+
 mcl_status mcl_run(mcl_ctx* c, const mcl_csc* A0, const int32_t* comp_offsets, int32_t ncomp,
                    const mcl_params* prm, int32_t* labels, int32_t* iters, double* chaos_hist,
                    mcl_csc* final_out, void* stream) {
@@ -892,7 +1075,83 @@ mcl_status mcl_run(mcl_ctx* c, const mcl_csc* A0, const int32_t* comp_offsets, i
     bool converged = false;
     const int saved_iter = c->iteration;
     c->prev_valid = 0;
+    PruneParams gpp;
+    const int gsizing = c->sizing >= 0 ? c->sizing : (prm->use_estimator ? 2 : 0);
+    bool graph_ok = batched && c->graph_mode && (gsizing == 0 || gsizing == 1) &&
+                    check_params(c, prm, &gpp, true) == MCL_OK;
+    GraphRun G;
+    int graph_at = -1;  // replay buffer holding cur
+    c->stats.graph_replays = 0;
     while (it < prm->max_iters) {
+        if (graph_ok && it >= 1) {
+            if (graph_at < 0) {
+                st = graph_prepare(c, prm, gpp, comp_offsets, ncomp, &cur, gsizing, G, s);
+                if (st) {
+                    graph_release(c, G, s, -1);
+                    c->iteration = saved_iter;
+                    return st;
+                }
+                graph_at = 0;
+                cur = G.buf[0];
+                cudaEvent_t e;
+                cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
+                cudaEventRecord(e, s);
+                cudaStreamWaitEvent(G.gs, e, 0);
+                cudaEventDestroy(e);
+            }
+            CUDA_TRY(c, cudaGraphLaunch(G.x[graph_at], G.gs));
+            count_launches((int)G.kernels);
+            CUDA_TRY(c, cudaStreamSynchronize(G.gs));
+            ++c->stats.graph_replays;
+            const unsigned ef = c->hctr->err;
+            if (ef & ERR_STAGING) {
+                // capacities beyond the replay buffers: this and later iterations run
+                // without graphs, from the replay buffer that holds the input
+                graph_ok = false;
+                int64_t nz = 0;
+                CUDA_TRY(c, cudaMemcpy(&nz, cur.colptr + cur.n, 8, cudaMemcpyDeviceToHost));
+                cur.nnz = nz;
+                CUDA_TRY(c, cudaMemcpy(hact.data(), c->comp_active.p, (size_t)ncomp,
+                                       cudaMemcpyDeviceToHost));
+                for (int q = 0; q < 2; ++q) {
+                    if (G.x[q]) cudaGraphExecDestroy(G.x[q]);
+                    if (G.g[q]) cudaGraphDestroy(G.g[q]);
+                    G.x[q] = nullptr;
+                    G.g[q] = nullptr;
+                }
+                free_csc(c, &G.buf[graph_at ^ 1], s);
+                G.buf[graph_at] = mcl_csc{};
+                cudaStreamDestroy(G.gs);
+                G.gs = nullptr;
+                graph_at = -1;
+                owned = true;
+                continue;
+            }
+            if (ef) {
+                graph_release(c, G, s, -1);
+                c->iteration = saved_iter;
+                return err_flags(c, ef);
+            }
+            graph_at ^= 1;
+            cur = G.buf[graph_at];
+            cur.nnz = (int64_t)c->hctr->nnz_out;
+            G.buf[graph_at].nnz = G.cap;
+            ch = chaos_from_bits(c->hctr->chaos_bits);
+            nactive = c->hctr->n_active;
+            mcl_stats& S = c->stats;
+            S.flops = (int64_t)c->hctr->flops;
+            S.nnz_in = G.cap;
+            S.nnz_b = (int64_t)c->hctr->nnz_b;
+            S.nnz_out = cur.nnz;
+            S.chaos = ch;
+            if (chaos_hist) chaos_hist[it] = ch;
+            ++it;
+            if (nactive == 0) {
+                converged = true;
+                break;
+            }
+            continue;
+        }
         mcl_csc nxt{};
         c->iteration = it + 1;
         const uint8_t* act = nullptr;
@@ -948,6 +1207,16 @@ mcl_status mcl_run(mcl_ctx* c, const mcl_csc* A0, const int32_t* comp_offsets, i
     }
     c->iteration = saved_iter;
     c->prev_valid = 0;
+    if (graph_at >= 0) {
+        // cur is replay buffer graph_at: keep it (owned, freed below or handed out)
+        cudaEvent_t e;
+        cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
+        cudaEventRecord(e, G.gs);
+        cudaStreamWaitEvent(s, e, 0);
+        cudaEventDestroy(e);
+        graph_release(c, G, s, graph_at);
+        owned = true;
+    }
     c->stats.iterations = it;
     if (iters) *iters = it;
     st = mcl_components(c, &cur, labels, stream);

@@ -31,6 +31,8 @@ struct DevCounters {
     int bin_fill[NBUCKET];
     int conf_ctr[NCONF];
     int work_ctr;
+    int n_active;                    // components still iterating (graph replay)
+    int pad2;
 };
 
 enum : unsigned {
@@ -41,6 +43,7 @@ enum : unsigned {
     ERR_INTERNAL = 16u,   // device consistency check failed
     ERR_TIMEOUT = 32u,    // bounded loop gave up
     ERR_CURSOR = 64u,     // cursor scratch too small
+    ERR_STAGING = 128u,   // output staging of a graph replay too small (nothing written)
 };
 
 struct CscView {
@@ -59,6 +62,11 @@ struct PruneParams {
     int32_t ksel;   // max(K, Krec)
     float r;
     int32_t inflate;
+    // tuning (autotuner): columns estimated at <= small_max entries use the
+    // small configuration; shape of the large one; rows planned per window
+    int32_t small_max;
+    int32_t table;
+    int32_t plan;
 };
 
 struct ExpandBuffers {
@@ -87,6 +95,7 @@ struct ExpandBuffers {
     int64_t scan_tmp_len;
     DevCounters* ctr;
     const uint8_t* active;  // optional per-column mask (NULL: all active)
+    int32_t nnz_is_bound;   // A.nnz is the capacity of A's arrays, not colptr[n]
 };
 
 // --- launch accounting (every launcher adds the kernels it starts) ---
@@ -109,11 +118,9 @@ void launch_cap_tighten(int32_t n, const int64_t* est, int64_t* cap, const uint8
 void launch_est_from_flops(const CscView& A, const ExpandBuffers& b, cudaStream_t s);
 void launch_binning(const CscView& A, const PruneParams& pp, const ExpandBuffers& b, int mask,
                     cudaStream_t s);
-int numeric_grid(int conf, int ksel, int num_sms);
-size_t numeric_smem(int conf, int ksel);
-int numeric_threads(int conf);
+int numeric_grid(int conf, const PruneParams& pp, int num_sms);
+size_t numeric_smem(int conf, const PruneParams& pp);
 constexpr int WINDOW_MAX = 4096;  // windows per column in bucket mode
-int conf_value_capacity(int conf);
 void launch_numeric(int conf, const CscView& A, const PruneParams& pp, const ExpandBuffers& b,
                     int grid, cudaStream_t s);
 void launch_compact(const CscView& A, const ExpandBuffers& b, const int64_t* colptr_out,
@@ -138,6 +145,9 @@ void launch_active_from_comp(int32_t n, const int32_t* comp_of_col, const uint8_
 void launch_fill_inactive(const CscView& A, const uint8_t* active, int32_t* kept, cudaStream_t s);
 void launch_comp_chaos(int32_t n, const int32_t* comp_of_col, const uint8_t* active,
                        const double* chaos, unsigned long long* comp_bits, cudaStream_t s);
+void launch_comp_retire(int32_t ncomp, const unsigned long long* comp_bits, double eps,
+                        uint8_t* comp_active, DevCounters* ctr, cudaStream_t s);
+void launch_staging_guard(DevCounters* ctr, int64_t capacity, cudaStream_t s);
 
 // --- estimator (mcl_estimator.cu) ---
 void launch_colmax_features(const CscView& A, int32_t iteration, const float* prev_logcf,

@@ -47,7 +47,8 @@ __global__ void k_colstats(CscView A, int32_t Krec, ExpandBuffers b) {
     unsigned long long fl_acc = 0, fl_max = 0;
     int deg_max = 0, span_max = 0;
     if (gw == 0 && lane == 0) {
-        if (A.colptr[0] != 0 || A.colptr[A.n] != A.nnz) set_err(C, ERR_COLPTR);
+        if (A.colptr[0] != 0 || (b.nnz_is_bound ? A.colptr[A.n] > A.nnz : A.colptr[A.n] != A.nnz))
+            set_err(C, ERR_COLPTR);
     }
     for (int64_t j = gw; j < A.n; j += nw) {
         const int64_t cb = A.colptr[j], ce = A.colptr[j + 1];
@@ -425,9 +426,10 @@ void launch_est_from_flops(const CscView& A, const ExpandBuffers& b, cudaStream_
 // Configuration 0 (small CTA) takes columns whose estimate fits one small
 // window's value capacity and whose span needs few windows; configuration 1
 // takes the rest.  The size class orders work longest-first by flops_j.
-__device__ __forceinline__ int bucket_of(int64_t est, int64_t flops, int span, int mask) {
+__device__ __forceinline__ int bucket_of(int64_t est, int64_t flops, int span, int mask,
+                                         int small_max) {
     int c = 1;
-    if ((mask & 1) && est <= 512 && span <= 8 * 16384) c = 0;
+    if ((mask & 1) && est <= small_max && span <= 8 * 16384) c = 0;
     if (!(mask & 2)) c = 0;
     int64_t f = flops >> 12;
     const int lg = f > 0 ? 63 - __clzll((long long)f) : 0;
@@ -435,7 +437,7 @@ __device__ __forceinline__ int bucket_of(int64_t est, int64_t flops, int span, i
     return c * NZ + z;
 }
 
-__global__ void k_bin_count(int32_t n, int mask, ExpandBuffers b) {
+__global__ void k_bin_count(int32_t n, int mask, int small_max, ExpandBuffers b) {
     __shared__ int hist[NBUCKET];
     for (int i = threadIdx.x; i < NBUCKET; i += blockDim.x) hist[i] = 0;
     __syncthreads();
@@ -445,7 +447,7 @@ __global__ void k_bin_count(int32_t n, int mask, ExpandBuffers b) {
             b.bucket[j] = -1;
             continue;
         }
-        int bk = bucket_of(b.est[j], b.flops[j], b.rhi[j] - b.rlo[j] + 1, mask);
+        int bk = bucket_of(b.est[j], b.flops[j], b.rhi[j] - b.rlo[j] + 1, mask, small_max);
         b.bucket[j] = bk;
         atomicAdd(&hist[bk], 1);
     }
@@ -490,7 +492,8 @@ void launch_binning(const CscView& A, const PruneParams& pp, const ExpandBuffers
     cudaMemsetAsync(b.ctr->bin_cnt, 0, sizeof(int) * NBUCKET, s);
     if (A.n > 0) {
         int64_t blocks = (A.n + 255) / 256;
-        k_bin_count<<<(unsigned)(blocks < 4096 ? blocks : 4096), 256, 0, s>>>(A.n, mask, b);
+        k_bin_count<<<(unsigned)(blocks < 4096 ? blocks : 4096), 256, 0, s>>>(A.n, mask, pp.small_max,
+                                                                               b);
         count_launches(1);
     }
     k_bin_offsets<<<1, 32, 0, s>>>(b.ctr);
@@ -523,6 +526,7 @@ void launch_prune_cap(const CscView& B, int32_t Krec, const ExpandBuffers& b, cu
 // final CSC (or, for a carried inactive column, the input column).
 __global__ void k_compact(CscView A, ExpandBuffers b, const int64_t* colptr_out, int32_t* row_out,
                           float* val_out) {
+    if (b.ctr->err & ERR_STAGING) return;  // the iteration is redone without the graph
     const int lane = threadIdx.x & 31;
     const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -781,6 +785,41 @@ void launch_comp_chaos(int32_t n, const int32_t* comp_of_col, const uint8_t* act
     if (n == 0) return;
     k_comp_chaos<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, comp_of_col, active, chaos,
                                                               comp_bits);
+    count_launches(1);
+}
+
+// Components whose chaos dropped below eps stop; the rest are counted.
+__global__ void k_comp_retire(int32_t ncomp, const unsigned long long* comp_bits, double eps,
+                              uint8_t* comp_active, DevCounters* ctr) {
+    if (ctr->err & ERR_STAGING) return;  // the iteration did not run; it is redone
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    int live = 0;
+    if (q < ncomp && comp_active[q]) {
+        if (__longlong_as_double((long long)comp_bits[q]) < eps)
+            comp_active[q] = 0;
+        else
+            live = 1;
+    }
+    live = __reduce_add_sync(FULL, live);
+    if ((threadIdx.x & 31) == 0 && live) atomicAdd(&ctr->n_active, live);
+}
+
+void launch_comp_retire(int32_t ncomp, const unsigned long long* comp_bits, double eps,
+                        uint8_t* comp_active, DevCounters* ctr, cudaStream_t s) {
+    if (ncomp <= 0) return;
+    k_comp_retire<<<(unsigned)((ncomp + 255) / 256), 256, 0, s>>>(ncomp, comp_bits, eps,
+                                                                   comp_active, ctr);
+    count_launches(1);
+}
+
+// Flags an output staging that cannot hold the capacities of this iteration
+// (the numeric pass and the compaction then write nothing).
+__global__ void k_staging_guard(DevCounters* ctr, int64_t capacity) {
+    if (threadIdx.x == 0 && (int64_t)ctr->cap_total > capacity) atomicOr(&ctr->err, ERR_STAGING);
+}
+
+void launch_staging_guard(DevCounters* ctr, int64_t capacity, cudaStream_t s) {
+    k_staging_guard<<<1, 32, 0, s>>>(ctr, capacity);
     count_launches(1);
 }
 

@@ -137,8 +137,8 @@ template <int T>
 __device__ void block_radix_sort_hi(uint64_t* s, uint64_t* tmp, int n, int bits, unsigned* whist,
                                     int* wsm) {
     constexpr int NW = T / 32;
-    constexpr int DPT = 256 / T;  // digits per thread in the offset scan
-    static_assert(256 % T == 0, "digits per thread");
+    constexpr int DPT = T >= 256 ? 1 : 256 / T;  // digits per thread in the offset scan
+    static_assert(T >= 256 ? T % 256 == 0 : 256 % T == 0, "digits per thread");
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int seg = ((n + NW - 1) / NW + 31) & ~31;
     const int w0 = min(n, warp * seg), w1 = min(n, w0 + seg);
@@ -160,24 +160,27 @@ __device__ void block_radix_sort_hi(uint64_t* s, uint64_t* tmp, int n, int bits,
         }
         __syncthreads();
         {
+            const bool own = tid * DPT < 256;  // threads beyond the 256 digits scan zeros
             unsigned c[DPT][NW];
             int tot = 0;
 #pragma unroll
             for (int q = 0; q < DPT; ++q)
 #pragma unroll
                 for (int w = 0; w < NW; ++w) {
-                    c[q][w] = whist[w * 256 + tid * DPT + q];
+                    c[q][w] = own ? whist[w * 256 + tid * DPT + q] : 0u;
                     tot += (int)c[q][w];
                 }
             int total;
             int run = block_scan_excl<T>(tot, &total, wsm);
+            if (own) {
 #pragma unroll
-            for (int q = 0; q < DPT; ++q)
+                for (int q = 0; q < DPT; ++q)
 #pragma unroll
-                for (int w = 0; w < NW; ++w) {
-                    whist[w * 256 + tid * DPT + q] = (unsigned)run;
-                    run += (int)c[q][w];
-                }
+                    for (int w = 0; w < NW; ++w) {
+                        whist[w * 256 + tid * DPT + q] = (unsigned)run;
+                        run += (int)c[q][w];
+                    }
+            }
         }
         __syncthreads();
         for (int base = w0; base < w1; base += 32) {
@@ -447,9 +450,10 @@ struct ExpandArgs {
     PruneParams pp;
     ExpandBuffers b;
     int conf;
+    int plan;
 };
 
-template <int T, int HS, int PLAN>
+template <int T, int HS>
 struct ExpandLayout {
     static constexpr size_t bytes(int ksel) {
         return (size_t)HS * 8 + (size_t)(ksel + HS) * 8 + 256 * 4 + 256 * 8 + sizeof(WinShared);
@@ -475,8 +479,9 @@ struct FastDiv {
     }
 };
 
-template <int T, int HS, int PLAN, int MINB>
+template <int T, int HS, int MINB>
 __global__ void __launch_bounds__(T, MINB) k_expand(ExpandArgs a) {
+    const int PLAN = a.plan;  // distinct rows a window is planned for
     constexpr int IPT = 8;
     static_assert(HS >= (T / 32) * 128, "the row sort's counters fit in the table");
     extern __shared__ __align__(16) unsigned char smem[];
@@ -497,6 +502,7 @@ __global__ void __launch_bounds__(T, MINB) k_expand(ExpandArgs a) {
     float* bval = b.bucket_val ? b.bucket_val + (int64_t)blockIdx.x * b.bucket_cap : nullptr;
     int32_t* woff = b.woff ? b.woff + (int64_t)blockIdx.x * (WINDOW_MAX + 1) : nullptr;
     const int wbeg = ctr->bin_off[a.conf * NZ], wend = ctr->bin_off[a.conf * NZ + NZ];
+    if (ctr->err & ERR_STAGING) return;  // the iteration is redone without the graph
 
     for (int i = tid; i < HS; i += T) tab[i] = SLOT_EMPTY;
     for (;;) {
@@ -893,43 +899,67 @@ __global__ void __launch_bounds__(T, MINB) k_expand(ExpandArgs a) {
     }
 }
 
-// configurations: 0 = small columns, 1 = everything else (threads, table
-// slots, planned entries per window, CTAs per SM)
-#define CONF0 128, 1024, 512, 8
-#define CONF1 256, 2048, 1024, 4
+// Configurations: 0 = small columns (128 threads, 1024 slots, windows of
+// 512 rows, 8 CTAs per SM); 1 = everything else, in one of three shapes
+// that the autotuner picks from (threads, table slots, CTAs per SM):
+//   table 0: 256 x 2048 x 4,  table 1: 512 x 4096 x 2,  table 2: 256 x 4096 x 2.
+// The candidate buffer holds ksel + HS keys (a window adds at most HS).
+template <int T_, int HS_, int MINB_>
+struct Conf {
+    static constexpr int T = T_, HS = HS_, MINB = MINB_;
+};
+using Conf0 = Conf<128, 1024, 8>;
+using Conf1a = Conf<256, 2048, 4>;
+using Conf1b = Conf<512, 4096, 2>;
+using Conf1c = Conf<256, 4096, 2>;
 
-size_t numeric_smem(int conf, int ksel) {
-    return conf == 0 ? ExpandLayout<128, 1024, 512>::bytes(ksel)
-                     : ExpandLayout<256, 2048, 1024>::bytes(ksel);
-}
+template <class C>
+static size_t conf_smem(int ksel) { return ExpandLayout<C::T, C::HS>::bytes(ksel); }
 
-int numeric_threads(int conf) { return conf == 0 ? 128 : 256; }
-
-int numeric_grid(int conf, int ksel, int num_sms) {
-    const size_t smem = numeric_smem(conf, ksel);
+template <class C>
+static int conf_grid(int ksel, int num_sms) {
+    const size_t smem = conf_smem<C>(ksel);
+    auto kern = k_expand<C::T, C::HS, C::MINB>;
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int occ = 0;
-    if (conf == 0) {
-        cudaFuncSetAttribute(k_expand<CONF0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_expand<CONF0>, 128, smem);
-    } else {
-        cudaFuncSetAttribute(k_expand<CONF1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_expand<CONF1>, 256, smem);
-    }
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, C::T, smem);
     if (occ < 1) occ = 1;
     return occ * num_sms;
 }
 
-// distinct rows one window of each configuration is planned for
-int conf_value_capacity(int conf) { return conf == 0 ? 512 : 1024; }
+template <class C>
+static void conf_launch(int conf, const CscView& A, const PruneParams& pp, const ExpandBuffers& b,
+                        int grid, cudaStream_t s) {
+    int plan = conf == 0 ? C::HS / 2 : (pp.plan > 0 ? pp.plan : C::HS / 2);
+    if (plan > (3 * C::HS) / 4) plan = (3 * C::HS) / 4;
+    if (plan < 64) plan = 64;
+    ExpandArgs a{A, pp, b, conf, plan};
+    k_expand<C::T, C::HS, C::MINB><<<grid, C::T, conf_smem<C>(pp.ksel), s>>>(a);
+}
+
+size_t numeric_smem(int conf, const PruneParams& pp) {
+    if (conf == 0) return conf_smem<Conf0>(pp.ksel);
+    return pp.table == 1 ? conf_smem<Conf1b>(pp.ksel)
+                         : pp.table == 2 ? conf_smem<Conf1c>(pp.ksel) : conf_smem<Conf1a>(pp.ksel);
+}
+
+int numeric_grid(int conf, const PruneParams& pp, int num_sms) {
+    if (conf == 0) return conf_grid<Conf0>(pp.ksel, num_sms);
+    return pp.table == 1 ? conf_grid<Conf1b>(pp.ksel, num_sms)
+                         : pp.table == 2 ? conf_grid<Conf1c>(pp.ksel, num_sms)
+                                         : conf_grid<Conf1a>(pp.ksel, num_sms);
+}
 
 void launch_numeric(int conf, const CscView& A, const PruneParams& pp, const ExpandBuffers& b,
                     int grid, cudaStream_t s) {
-    ExpandArgs a{A, pp, b, conf};
-    const size_t smem = numeric_smem(conf, pp.ksel);
     if (conf == 0)
-        k_expand<CONF0><<<grid, 128, smem, s>>>(a);
+        conf_launch<Conf0>(conf, A, pp, b, grid, s);
+    else if (pp.table == 1)
+        conf_launch<Conf1b>(conf, A, pp, b, grid, s);
+    else if (pp.table == 2)
+        conf_launch<Conf1c>(conf, A, pp, b, grid, s);
     else
-        k_expand<CONF1><<<grid, 256, smem, s>>>(a);
+        conf_launch<Conf1a>(conf, A, pp, b, grid, s);
     count_launches(1);
 }
 

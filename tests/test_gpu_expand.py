@@ -360,3 +360,42 @@ def test_column_batched_expansion_equals_single_pass(ctx, budget):
     cols = np.random.default_rng(5).choice(A.n, 500, replace=False).astype(np.int32)
     rep, _ = compare_iteration(A, out.to_host(), _oprm(prm), cols=cols, rtol=RTOL)
     assert rep.ok(), rep.failures[:5]
+
+
+@pytest.mark.parametrize("cap", [0, 1])
+def test_batched_graph_replay_matches_eager(ctx, cap):
+    """Batched MCL with iterations after the first replayed as CUDA graphs
+    gives the same iterations, clusters and chaos history as the eager
+    loop; cap 1 shrinks the replay buffers below an iteration's capacities,
+    so that the device guard stops the replay and the host finishes
+    without graphs."""
+    from paper_2002_10083_gb300 import mcl
+    A = synth.component_batch(ncomp=16, size_lo=50, size_hi=1200, p_in=0.3, p_out=0.002,
+                              seed=4).with_val32()
+    offs = A.comp_offsets
+    prm = _prm(theta=1e-4, K=200, p=0.9, iters=40)
+    prm.batched = 1
+    try:
+        ctx.set_option(mcl.OPT_GRAPH, 0)
+        lab0, it0, hist0, _, nc0 = ctx.run(_dev(A), prm, comp_offsets=offs, keep_final=False)
+        assert ctx.stats()["graph_replays"] == 0
+        ctx.set_option(mcl.OPT_GRAPH, 1)
+        ctx.set_option(mcl.OPT_GRAPH_CAP, cap)
+        lab1, it1, hist1, _, nc1 = ctx.run(_dev(A), prm, comp_offsets=offs, keep_final=False)
+        replays = ctx.stats()["graph_replays"]
+    finally:
+        ctx.set_option(mcl.OPT_GRAPH, 1)
+        ctx.set_option(mcl.OPT_GRAPH_CAP, 0)
+    assert not nc0 and not nc1
+    assert it0 == it1 and it1 > 2
+    assert replays >= 1
+    if cap == 0:
+        assert replays == it1 - 1
+    assert np.array_equal(lab0.cpu().numpy(), lab1.cpu().numpy())
+    # FP32 atomic accumulation orders differ from run to run, graph or not, and
+    # the matrices of later iterations inherit those last-bit differences
+    np.testing.assert_allclose(hist1[:it1], hist0[:it0], rtol=1e-3, atol=2e-4)
+    # and the per-component oracle
+    _, o_iters, _, o_lab = oracle.run_mcl(A, _oprm(prm), per_component=offs)
+    assert it1 == max(o_iters)
+    assert np.array_equal(lab1.cpu().numpy(), o_lab)
