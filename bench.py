@@ -379,6 +379,9 @@ def run_batched(args):
                                           val=A.val.astype(np.float32)))
     ctx = mcl.Context(0)
     estimator.install(ctx)
+    from paper_2002_10083_gb300 import autotune
+    tuned = autotune.apply(ctx, autotune.load(), torch.cuda.get_device_name(0),
+                           autotune.class_of_host(A))
     if args.phase_budget_gb:
         ctx.set_option(mcl.OPT_PHASE_BUDGET, int(args.phase_budget_gb * (1 << 30)))
     torch.cuda.synchronize()
@@ -408,6 +411,7 @@ def run_batched(args):
                                                   "estimator_misses")},
             "generation_s": round(gen_s, 1), "form": "learned" if prm.use_estimator else "plain",
             "phase_budget_gb": args.phase_budget_gb,
+            "tuning": tuned if tuned is not None else "library defaults",
             "graph_replays": int(st["graph_replays"]),
             "eager": {"ms_total": round(ms_e, 1), "iters_per_s": round(iters_e / (ms_e / 1000.0), 4),
                       "iterations": iters_e},

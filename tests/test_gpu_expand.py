@@ -399,3 +399,36 @@ def test_batched_graph_replay_matches_eager(ctx, cap):
     _, o_iters, _, o_lab = oracle.run_mcl(A, _oprm(prm), per_component=offs)
     assert it1 == max(o_iters)
     assert np.array_equal(lab1.cpu().numpy(), o_lab)
+
+
+@pytest.mark.slow
+def test_zipf4m_degree_law_column_batched_sampled():
+    """The 4M-vertex workload's degree law (Zipf(2), mean 120, capped at
+    5,000) at a quarter of its vertices, expanded in column batches under a
+    small staging budget: sampled columns (the hubs included) against the
+    oracle, every output column sums to 1."""
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2002_10083_gb300 import estimator, mcl
+    A = synth.config("zipf4m", n=1_000_000).with_val32()
+    ctx = mcl.Context(0)
+    try:
+        estimator.install(ctx)
+        ctx.set_option(mcl.OPT_PHASE_BUDGET, 2 << 30)
+        prm = _prm(theta=1e-4, K=1100, p=0.9)
+        prm.use_estimator = 1
+        out, ch = ctx.expand(_dev(A), prm)
+        assert ctx.stats()["phases"] > 1
+        torch.cuda.synchronize()
+        G = out.to_host()
+    finally:
+        ctx.close()
+    sums = np.add.reduceat(G.val, G.colptr[:-1]) if G.nnz else np.zeros(0)
+    nzc = np.diff(G.colptr) > 0
+    np.testing.assert_allclose(sums[nzc], 1.0, rtol=0, atol=2e-5)
+    deg = np.diff(A.colptr)
+    rng = np.random.default_rng(2004)
+    cols = np.concatenate([rng.choice(A.n, 600, replace=False),
+                           np.argsort(-deg)[:20]]).astype(np.int32)
+    rep, _ = compare_iteration(A, G, _oprm(prm), cols=cols, rtol=RTOL)
+    assert rep.ok(), rep.failures[:5]
