@@ -386,36 +386,55 @@ def run_batched(args):
         ctx.set_option(mcl.OPT_PHASE_BUDGET, int(args.phase_budget_gb * (1 << 30)))
     torch.cuda.synchronize()
 
-    def timed_run(graph: int):
+    def timed_run(graph: int, offsets, use_est: int):
         ctx.set_option(mcl.OPT_GRAPH, graph)
+        p = mcl.Params(threshold=prm.threshold, select_k=prm.select_k,
+                       recover_pct=prm.recover_pct, inflation=prm.inflation,
+                       chaos_eps=prm.chaos_eps, max_iters=prm.max_iters,
+                       batched=1 if offsets is not None else 0, use_estimator=use_est)
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record()
-        out = ctx.run(D, prm, comp_offsets=offs, keep_final=False)
+        out = ctx.run(D, p, comp_offsets=offsets, keep_final=False)
         e1.record()
         torch.cuda.synchronize()
         return out, e0.elapsed_time(e1), ctx.stats()
 
-    # eager loop (host decisions between the launches of an iteration), then
-    # the same run with iterations after the first replayed as CUDA graphs
-    (lab_e, iters_e, hist_e, _, nc_e), ms_e, st_e = timed_run(0)
-    (lab, iters, hist, final, notconv), ms, st = timed_run(1)
-    same = bool(torch.equal(lab, lab_e)) and iters == iters_e
+    def summary(res, ms, st):
+        lab_, iters_, hist_, _, nc_ = res
+        return {"ms_total": round(ms, 1), "iterations": iters_,
+                "iters_per_s": round(iters_ / (ms / 1000.0), 4), "converged": not nc_,
+                "graph_replays": int(st["graph_replays"])}
+
+    forms = {}
+    if offs is not None:
+        # plain: the whole block-diagonal matrix until its global chaos < eps,
+        # exact sizing, eager loop; batched: per-component retirement with
+        # iterations after the first replayed as CUDA graphs (exact sizing),
+        # then eager, then with the learned sizing
+        runs = [("plain", 0, None, 0), ("batched", 1, offs, 0), ("batched_eager", 0, offs, 0),
+                ("learned_batched", 1, offs, 1)]
+    else:
+        runs = [("learned", 1, None, prm.use_estimator)]
+    results = {}
+    for name, graph, o, ue in runs:
+        res, ms, st = timed_run(graph, o, ue)
+        results[name] = (res, ms, st)
+        forms[name] = summary(res, ms, st)
+    main_name = "learned_batched" if offs is not None else "learned"
+    (lab, iters, hist, final, notconv), ms, st = results[main_name]
+    labels_equal = {k: bool(torch.equal(v[0][0], lab)) for k, v in results.items()}
     line = {"metric": METRIC, "workload": args.workload, "n": A.n, "nnz": A.nnz,
             "components": None if offs is None else len(offs) - 1,
-            "iterations": iters, "converged": not notconv, "ms_total": round(ms, 1),
-            "iters_per_s": round(iters / (ms / 1000.0), 4),
+            "form": main_name, "iterations": iters, "converged": not notconv,
+            "ms_total": round(ms, 1), "iters_per_s": round(iters / (ms / 1000.0), 4),
             "chaos_history": [round(h, 6) for h in hist],
             "clusters": int(len(np.unique(lab.cpu().numpy()))),
             "last_iteration": {k: st[k] for k in ("flops", "nnz_b", "nnz_out", "phases",
                                                   "estimator_misses")},
-            "generation_s": round(gen_s, 1), "form": "learned" if prm.use_estimator else "plain",
-            "phase_budget_gb": args.phase_budget_gb,
-            "tuning": tuned if tuned is not None else "library defaults",
-            "graph_replays": int(st["graph_replays"]),
-            "eager": {"ms_total": round(ms_e, 1), "iters_per_s": round(iters_e / (ms_e / 1000.0), 4),
-                      "iterations": iters_e},
-            "graph_equals_eager": same}
+            "forms": forms, "labels_equal_to_main": labels_equal,
+            "generation_s": round(gen_s, 1), "phase_budget_gb": args.phase_budget_gb,
+            "tuning": tuned if tuned is not None else "library defaults"}
     print(json.dumps(line), flush=True)
     return 0
 

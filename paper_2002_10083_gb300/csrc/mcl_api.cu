@@ -49,7 +49,7 @@ struct mcl_ctx {
     int plan = 0;           // autotuned: rows planned per window (0: half the table)
     int64_t graph_cap = 0;  // entries of the replay buffers (0: per-component bound)
     // learned estimator (weights on device)
-    Buf mlp_w, mlp_norm, colmax, feats, prev_logcf;
+    Buf mlp_w, mlp_norm, colmax, feats, prev_logcf, iter_dev;
     int has_estimator = 0;
     float est_safety = 1.25f;
     int iteration = 1;
@@ -290,7 +290,8 @@ void mcl_destroy(mcl_ctx* c) {
                   &c->flops, &c->colsum, &c->rlo, &c->rhi,  &c->cap,     &c->off,  &c->est,
                   &c->bucket, &c->work,   &c->kept,    &c->chaos,   &c->bnnz, &c->tmp_row,
                   &c->tmp_val, &c->cursors, &c->scan,  &c->ctr,     &c->active, &c->mlp_w,
-                  &c->mlp_norm, &c->colmax, &c->feats, &c->prev_logcf, &c->cohen_m, &c->cohen_e};
+                  &c->mlp_norm, &c->colmax, &c->feats, &c->prev_logcf, &c->cohen_m, &c->cohen_e,
+                  &c->iter_dev};
     for (Buf* b : all) dev_free(c, b->p, 0);
     cudaDeviceSynchronize();
     for (auto& e : c->ev) cudaEventDestroy(e);
@@ -930,10 +931,20 @@ static void static_iteration(mcl_ctx* c, const mcl_params* prm, const PruneParam
     const int grid_max = max_numeric_grid(c, pp);
     if (sizing == 1) {
         launch_est_from_flops(Av, b, s);
+    } else if (sizing == 2) {  // learned: features (iteration index on the device) -> MLP
+        launch_colmax_features(Av, 0, (const float*)c->prev_logcf.p, (float*)c->colmax.p,
+                               (float*)c->feats.p, s, (const int32_t*)c->iter_dev.p);
+        launch_mlp_forward((const float*)c->feats.p, n, (const uint16_t*)c->mlp_w.p,
+                           (const float*)c->mlp_norm.p, nullptr, b.est, c->est_safety, b.flops,
+                           b.rlo, b.rhi, s);
+    } else if (sizing == 3) {
+        launch_cohen(Av, c->cohen_r, c->cohen_seed, (float*)c->cohen_m.p, (float*)c->cohen_e.p, s);
+        launch_cohen_to_est(n, (const float*)c->cohen_e.p, 1.0f, b, s);
     } else {
         launch_symbolic(Av, b, b.est, c->num_sms, grid_max, s);
         launch_cap_tighten(n, b.est, b.cap, b.active, s);
     }
+    if (c->est_milli != 1000) launch_scale_est(n, b.est, c->est_milli, s);
     launch_exclusive_scan<int64_t>(b.cap, n, b.off, b.scan_tmp, &b.ctr->cap_total, s);
     launch_staging_guard(b.ctr, cap, s);
     launch_binning(Av, pp, b, c->conf_mask, s);
@@ -958,6 +969,10 @@ static void static_iteration(mcl_ctx* c, const mcl_params* prm, const PruneParam
                       (unsigned long long*)c->comp_bits.p, s);
     launch_comp_retire(ncomp, (const unsigned long long*)c->comp_bits.p, prm->chaos_eps,
                        (uint8_t*)c->comp_active.p, b.ctr, s);
+    if (sizing == 2) {  // this iteration's compression factors feed the next one's features
+        launch_logcf(n, b.flops, b.bnnz, (float*)c->prev_logcf.p, s);
+        launch_iter_bump((int32_t*)c->iter_dev.p, s);
+    }
     cudaMemcpyAsync(c->hctr, c->ctr.p, sizeof(DevCounters), cudaMemcpyDeviceToHost, s);
 }
 
@@ -982,10 +997,23 @@ static mcl_status graph_prepare(mcl_ctx* c, const mcl_params* prm, const PrunePa
     int64_t capb = (int64_t)pp.Krec * pp.Krec;
     const int64_t capb_max = (int64_t)(c->bucket_budget / ((size_t)g1 * 8));
     if (capb > capb_max) capb = capb_max;
+    const size_t n1 = (size_t)n + 1;
     if (!ensure(c, c->tmp_row, (size_t)cap * 4 + 4, s) || !ensure(c, c->tmp_val, (size_t)cap * 4 + 4, s) ||
         !ensure(c, c->cursors, (size_t)grid_max * 6 * stride * 4, s) ||
         !ensure(c, c->comp_bits, (size_t)ncomp * 8, s))
         return fail(c, MCL_ERR_OOM, "graph replay scratch allocation failed");
+    if (sizing == 2) {
+        if (!c->has_estimator) return fail(c, MCL_ERR_INVALID, "use_estimator set but no estimator loaded");
+        if (!ensure(c, c->colmax, n1 * 4, s) || !ensure(c, c->feats, n1 * 4 * MCL_NFEATURES, s) ||
+            !ensure(c, c->prev_logcf, n1 * 4, s) || !ensure(c, c->iter_dev, 4, s))
+            return fail(c, MCL_ERR_OOM, "estimator scratch allocation failed");
+        // the first replay is iteration 2; the logs of cf of iteration 1 are in prev_logcf
+        const int32_t it2 = 2;
+        CUDA_TRY(c, cudaMemcpyAsync(c->iter_dev.p, &it2, 4, cudaMemcpyHostToDevice, s));
+    } else if (sizing == 3) {
+        if (!ensure(c, c->cohen_m, n1 * c->cohen_r * 4, s) || !ensure(c, c->cohen_e, n1 * 4, s))
+            return fail(c, MCL_ERR_OOM, "estimator scratch allocation failed");
+    }
     if (capb >= 1024 && ensure(c, c->bucket_row, (size_t)g1 * capb * 4, s) &&
         ensure(c, c->bucket_val, (size_t)g1 * capb * 4, s) &&
         ensure(c, c->woff, (size_t)g1 * (WINDOW_MAX + 1) * 4, s)) {
@@ -1077,7 +1105,7 @@ mcl_status mcl_run(mcl_ctx* c, const mcl_csc* A0, const int32_t* comp_offsets, i
     c->prev_valid = 0;
     PruneParams gpp;
     const int gsizing = c->sizing >= 0 ? c->sizing : (prm->use_estimator ? 2 : 0);
-    bool graph_ok = batched && c->graph_mode && (gsizing == 0 || gsizing == 1) &&
+    bool graph_ok = batched && c->graph_mode && gsizing >= 0 && gsizing <= 3 &&
                     check_params(c, prm, &gpp, true) == MCL_OK;
     GraphRun G;
     int graph_at = -1;  // replay buffer holding cur

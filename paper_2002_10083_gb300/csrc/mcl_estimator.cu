@@ -49,8 +49,9 @@ __global__ void k_colmax(CscView A, float* colmax) {
 }
 
 // Warp per column: the 16 features (see oracle/mlp.py FEATURES for the list).
-__global__ void k_features(CscView A, int32_t iteration, const float* prev_logcf,
-                           const float* colmax, float* feats) {
+__global__ void k_features(CscView A, int32_t iteration, const int32_t* iter_dev,
+                           const float* prev_logcf, const float* colmax, float* feats) {
+    if (iter_dev) iteration = *iter_dev;  // graph replays keep the index on the device
     const int lane = threadIdx.x & 31;
     const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -327,13 +328,13 @@ __global__ void k_logcf(int32_t n, const int64_t* flops, const int64_t* bnnz, fl
 }
 
 void launch_colmax_features(const CscView& A, int32_t iteration, const float* prev_logcf,
-                            float* colmax, float* feats, cudaStream_t s) {
+                            float* colmax, float* feats, cudaStream_t s, const int32_t* iter_dev) {
     if (A.n == 0) return;
     int64_t blocks = ((int64_t)A.n * 32 + 255) / 256;
     if (blocks > 152 * 16) blocks = 152 * 16;
     k_colmax<<<(unsigned)blocks, 256, 0, s>>>(A, colmax);
     count_launches(1);
-    k_features<<<(unsigned)blocks, 256, 0, s>>>(A, iteration, prev_logcf, colmax, feats);
+    k_features<<<(unsigned)blocks, 256, 0, s>>>(A, iteration, iter_dev, prev_logcf, colmax, feats);
     count_launches(1);
 }
 
@@ -363,6 +364,15 @@ void launch_mlp_backward(const float* feats, const float* targets, int64_t n,
 void launch_adam(float* master, float* m, float* v, const float* grad, int64_t step, float lr,
                  float b1, float b2, float eps, uint16_t* wbits, cudaStream_t s) {
     k_adam<<<(NPARAM + 255) / 256, 256, 0, s>>>(master, m, v, grad, step, lr, b1, b2, eps, wbits);
+    count_launches(1);
+}
+
+__global__ void k_iter_bump(int32_t* it) {
+    if (threadIdx.x == 0) ++*it;
+}
+
+void launch_iter_bump(int32_t* it, cudaStream_t s) {
+    k_iter_bump<<<1, 32, 0, s>>>(it);
     count_launches(1);
 }
 

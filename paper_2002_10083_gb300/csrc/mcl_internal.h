@@ -151,7 +151,9 @@ void launch_staging_guard(DevCounters* ctr, int64_t capacity, cudaStream_t s);
 
 // --- estimator (mcl_estimator.cu) ---
 void launch_colmax_features(const CscView& A, int32_t iteration, const float* prev_logcf,
-                            float* colmax, float* feats, cudaStream_t s);
+                            float* colmax, float* feats, cudaStream_t s,
+                            const int32_t* iter_dev = nullptr);
+void launch_iter_bump(int32_t* it, cudaStream_t s);
 void launch_mlp_forward(const float* feats, int64_t n, const uint16_t* wbits, const float* norm,
                         float* out, int64_t* est, float safety, const int64_t* flops,
                         const int32_t* rlo, const int32_t* rhi, cudaStream_t s);

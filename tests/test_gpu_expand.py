@@ -362,8 +362,8 @@ def test_column_batched_expansion_equals_single_pass(ctx, budget):
     assert rep.ok(), rep.failures[:5]
 
 
-@pytest.mark.parametrize("cap", [0, 1])
-def test_batched_graph_replay_matches_eager(ctx, cap):
+@pytest.mark.parametrize("cap,learned", [(0, False), (1, False), (0, True)])
+def test_batched_graph_replay_matches_eager(ctx, cap, learned):
     """Batched MCL with iterations after the first replayed as CUDA graphs
     gives the same iterations, clusters and chaos history as the eager
     loop; cap 1 shrinks the replay buffers below an iteration's capacities,
@@ -375,6 +375,10 @@ def test_batched_graph_replay_matches_eager(ctx, cap):
     offs = A.comp_offsets
     prm = _prm(theta=1e-4, K=200, p=0.9, iters=40)
     prm.batched = 1
+    if learned:  # learned sizing: features and MLP inside the replayed graph
+        from paper_2002_10083_gb300 import estimator
+        estimator.install(ctx)
+        prm.use_estimator = 1
     try:
         ctx.set_option(mcl.OPT_GRAPH, 0)
         lab0, it0, hist0, _, nc0 = ctx.run(_dev(A), prm, comp_offsets=offs, keep_final=False)
