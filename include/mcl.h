@@ -108,6 +108,9 @@ typedef struct {
     int32_t iterations;
     int32_t phases;           /* column batches of the last mcl_expand */
     int32_t graph_replays;    /* iterations of the last batched mcl_run replayed as CUDA graphs */
+    int32_t exact_from;       /* mcl_run with use_estimator: first iteration sized exactly because
+                                 the learned estimates of an earlier one fell short on more than
+                                 1/20 of its columns (0: none) */
 } mcl_stats;
 
 /* Create a context on `device` (made current by every call).  alloc/free

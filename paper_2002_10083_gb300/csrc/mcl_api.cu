@@ -40,6 +40,7 @@ struct mcl_ctx {
     cudaEvent_t ev[8] = {};
     // options
     int sizing = -1;        // -1: from params (exact or learned); 0 exact; 1 flops bound
+    int run_exact = 0;      // mcl_run: learned estimates missed too often, size exactly
     int conf_mask = 0x3;    // numeric configurations allowed
     int validate = 1;
     int est_milli = 1000;   // estimate scale (test knob)
@@ -394,7 +395,8 @@ static mcl_status expand_impl(mcl_ctx* c, const mcl_csc* A, const mcl_params* pr
         return fail(c, MCL_ERR_OOM, "cursor scratch allocation failed");
     b.cursors = (int32_t*)c->cursors.p;
     // ---- size estimate ----
-    const int sizing = c->sizing >= 0 ? c->sizing : (prm->use_estimator ? 2 : 0);
+    const int sizing =
+        c->sizing >= 0 ? c->sizing : (prm->use_estimator && !c->run_exact ? 2 : 0);
     if (sizing == 2) {
         if (!c->has_estimator)
             return fail(c, MCL_ERR_INVALID, "use_estimator set but no estimator loaded");
@@ -1104,12 +1106,27 @@ mcl_status mcl_run(mcl_ctx* c, const mcl_csc* A0, const int32_t* comp_offsets, i
     const int saved_iter = c->iteration;
     c->prev_valid = 0;
     PruneParams gpp;
-    const int gsizing = c->sizing >= 0 ? c->sizing : (prm->use_estimator ? 2 : 0);
+    c->run_exact = 0;
+    int gsizing = c->sizing >= 0 ? c->sizing : (prm->use_estimator ? 2 : 0);
+    // Estimator fallback: an iteration whose learned estimates fall short on
+    // more than 1/20 of the expanded columns (each miss splits windows and
+    // redoes their products) hands the rest of the run to the exact sizing.
+    auto learned_missed = [&](int64_t misses) -> bool {
+        if (gsizing != 2 || c->run_exact) return false;
+        int64_t cols = cur.n;
+        if (batched) {
+            cols = 0;
+            for (int q = 0; q < ncomp; ++q)
+                if (hact[q]) cols += comp_offsets[q + 1] - comp_offsets[q];
+        }
+        return misses * 20 > cols;
+    };
     bool graph_ok = batched && c->graph_mode && gsizing >= 0 && gsizing <= 3 &&
                     check_params(c, prm, &gpp, true) == MCL_OK;
     GraphRun G;
     int graph_at = -1;  // replay buffer holding cur
     c->stats.graph_replays = 0;
+    c->stats.exact_from = 0;
     while (it < prm->max_iters) {
         if (graph_ok && it >= 1) {
             if (graph_at < 0) {
@@ -1117,6 +1134,7 @@ mcl_status mcl_run(mcl_ctx* c, const mcl_csc* A0, const int32_t* comp_offsets, i
                 if (st) {
                     graph_release(c, G, s, -1);
                     c->iteration = saved_iter;
+                    c->run_exact = 0;
                     return st;
                 }
                 graph_at = 0;
@@ -1132,6 +1150,7 @@ mcl_status mcl_run(mcl_ctx* c, const mcl_csc* A0, const int32_t* comp_offsets, i
             CUDA_TRY(c, cudaStreamSynchronize(G.gs));
             ++c->stats.graph_replays;
             const unsigned ef = c->hctr->err;
+            const bool refit = !ef && learned_missed((int64_t)c->hctr->misses);
             if (ef & ERR_STAGING) {
                 // capacities beyond the replay buffers: this and later iterations run
                 // without graphs, from the replay buffer that holds the input
@@ -1158,6 +1177,7 @@ mcl_status mcl_run(mcl_ctx* c, const mcl_csc* A0, const int32_t* comp_offsets, i
             if (ef) {
                 graph_release(c, G, s, -1);
                 c->iteration = saved_iter;
+                c->run_exact = 0;
                 return err_flags(c, ef);
             }
             graph_at ^= 1;
@@ -1166,6 +1186,27 @@ mcl_status mcl_run(mcl_ctx* c, const mcl_csc* A0, const int32_t* comp_offsets, i
             G.buf[graph_at].nnz = G.cap;
             ch = chaos_from_bits(c->hctr->chaos_bits);
             nactive = c->hctr->n_active;
+            if (refit && nactive > 0) {
+                // later replays size exactly: recapture from the buffer holding cur
+                c->run_exact = 1;
+                c->stats.exact_from = it + 2;
+                gsizing = 0;
+                CUDA_TRY(c, cudaMemcpy(hact.data(), c->comp_active.p, (size_t)ncomp,
+                                       cudaMemcpyDeviceToHost));
+                for (int q = 0; q < 2; ++q) {
+                    if (G.x[q]) cudaGraphExecDestroy(G.x[q]);
+                    if (G.g[q]) cudaGraphDestroy(G.g[q]);
+                    G.x[q] = nullptr;
+                    G.g[q] = nullptr;
+                }
+                CUDA_TRY(c, cudaStreamSynchronize(G.gs));
+                cudaStreamDestroy(G.gs);
+                G.gs = nullptr;
+                free_csc(c, &G.buf[graph_at ^ 1], s);
+                G.buf[graph_at] = mcl_csc{};
+                graph_at = -1;
+                owned = true;
+            }
             mcl_stats& S = c->stats;
             S.flops = (int64_t)c->hctr->flops;
             S.nnz_in = G.cap;
@@ -1189,6 +1230,7 @@ mcl_status mcl_run(mcl_ctx* c, const mcl_csc* A0, const int32_t* comp_offsets, i
             act = (const uint8_t*)c->active.p;
         }
         st = expand_impl(c, &cur, prm, &nxt, &ch, s, act);
+        const int64_t it_misses = st ? 0 : c->stats.estimator_misses;
         if (!st && batched) {
             // per-component chaos of this iteration; converged components retire
             cudaMemsetAsync(c->comp_bits.p, 0, (size_t)ncomp * 8, s);
@@ -1209,6 +1251,11 @@ mcl_status mcl_run(mcl_ctx* c, const mcl_csc* A0, const int32_t* comp_offsets, i
             if (!st)
                 cudaMemcpyAsync(c->comp_active.p, hact.data(), (size_t)ncomp, cudaMemcpyHostToDevice, s);
         }
+        if (!st && learned_missed(it_misses)) {
+            c->run_exact = 1;
+            c->stats.exact_from = it + 2;
+            gsizing = 0;
+        }
         if (!st && prm->use_estimator) {
             // the compression factor of this iteration feeds the next one's features
             if (ensure(c, c->prev_logcf, ((size_t)cur.n + 1) * 4, s)) {
@@ -1220,6 +1267,7 @@ mcl_status mcl_run(mcl_ctx* c, const mcl_csc* A0, const int32_t* comp_offsets, i
         if (st) {
             if (owned) free_csc(c, &cur, s);
             c->iteration = saved_iter;
+            c->run_exact = 0;
             c->prev_valid = 0;
             return st;
         }
@@ -1234,6 +1282,7 @@ mcl_status mcl_run(mcl_ctx* c, const mcl_csc* A0, const int32_t* comp_offsets, i
         }
     }
     c->iteration = saved_iter;
+    c->run_exact = 0;
     c->prev_valid = 0;
     if (graph_at >= 0) {
         // cur is replay buffer graph_at: keep it (owned, freed below or handed out)

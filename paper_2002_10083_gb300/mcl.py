@@ -57,7 +57,7 @@ class _Stats(ctypes.Structure):
                 ("ms_compact", ctypes.c_float), ("ms_chaos", ctypes.c_float),
                 ("ms_total", ctypes.c_float), ("bins_used", ctypes.c_int32),
                 ("iterations", ctypes.c_int32), ("phases", ctypes.c_int32),
-                ("graph_replays", ctypes.c_int32)]
+                ("graph_replays", ctypes.c_int32), ("exact_from", ctypes.c_int32)]
 
 
 _ALLOC = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)

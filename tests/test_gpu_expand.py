@@ -362,8 +362,9 @@ def test_column_batched_expansion_equals_single_pass(ctx, budget):
     assert rep.ok(), rep.failures[:5]
 
 
-@pytest.mark.parametrize("cap,learned", [(0, False), (1, False), (0, True)])
-def test_batched_graph_replay_matches_eager(ctx, cap, learned):
+@pytest.mark.parametrize("cap,learned,scale", [(0, False, 1000), (1, False, 1000),
+                                               (0, True, 1000), (0, True, 20)])
+def test_batched_graph_replay_matches_eager(ctx, cap, learned, scale):
     """Batched MCL with iterations after the first replayed as CUDA graphs
     gives the same iterations, clusters and chaos history as the eager
     loop; cap 1 shrinks the replay buffers below an iteration's capacities,
@@ -380,16 +381,24 @@ def test_batched_graph_replay_matches_eager(ctx, cap, learned):
         estimator.install(ctx)
         prm.use_estimator = 1
     try:
+        # scale 20: every learned estimate 50x too small, so that the run
+        # falls back to exact sizing after the first iteration
+        ctx.set_option(mcl.OPT_EST_SCALE, scale)
         ctx.set_option(mcl.OPT_GRAPH, 0)
         lab0, it0, hist0, _, nc0 = ctx.run(_dev(A), prm, comp_offsets=offs, keep_final=False)
-        assert ctx.stats()["graph_replays"] == 0
+        st0 = ctx.stats()
+        assert st0["graph_replays"] == 0
         ctx.set_option(mcl.OPT_GRAPH, 1)
         ctx.set_option(mcl.OPT_GRAPH_CAP, cap)
         lab1, it1, hist1, _, nc1 = ctx.run(_dev(A), prm, comp_offsets=offs, keep_final=False)
-        replays = ctx.stats()["graph_replays"]
+        st1 = ctx.stats()
+        replays = st1["graph_replays"]
     finally:
         ctx.set_option(mcl.OPT_GRAPH, 1)
         ctx.set_option(mcl.OPT_GRAPH_CAP, 0)
+        ctx.set_option(mcl.OPT_EST_SCALE, 1000)
+    if scale < 1000:
+        assert st0["exact_from"] == 2 and st1["exact_from"] == 2
     assert not nc0 and not nc1
     assert it0 == it1 and it1 > 2
     assert replays >= 1
