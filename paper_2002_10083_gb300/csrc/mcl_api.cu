@@ -1212,6 +1212,8 @@ mcl_status mcl_run(mcl_ctx* c, const mcl_csc* A0, const int32_t* comp_offsets, i
             S.nnz_in = G.cap;
             S.nnz_b = (int64_t)c->hctr->nnz_b;
             S.nnz_out = cur.nnz;
+            S.estimator_misses = (int64_t)c->hctr->misses;
+            S.range_splits = (int64_t)c->hctr->splits;
             S.chaos = ch;
             if (chaos_hist) chaos_hist[it] = ch;
             ++it;
