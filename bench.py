@@ -386,7 +386,11 @@ def run_batched(args):
     D = mcl.DeviceCSC.from_host(synth.CSC(n=A.n, colptr=A.colptr, rowidx=A.rowidx,
                                           val=A.val.astype(np.float32)))
     ctx = mcl.Context(0)
-    estimator.install(ctx)
+    # the estimator trained on this workload's graph family (other seeds), if there is one
+    est_path = args.estimator or (estimator.BATCH_WEIGHTS if args.workload == "batch4096" and
+                                  os.path.exists(estimator.BATCH_WEIGHTS)
+                                  else estimator.DEFAULT_WEIGHTS)
+    est_meta = estimator.install(ctx, est_path)
     from paper_2002_10083_gb300 import autotune
     tuned = autotune.apply(ctx, autotune.load(), torch.cuda.get_device_name(0),
                            autotune.class_of_host(A))
@@ -442,7 +446,10 @@ def run_batched(args):
                                                   "estimator_misses")},
             "forms": forms, "labels_equal_to_main": labels_equal,
             "generation_s": round(gen_s, 1), "phase_budget_gb": args.phase_budget_gb,
-            "tuning": tuned if tuned is not None else "library defaults"}
+            "tuning": tuned if tuned is not None else "library defaults",
+            "estimator": {"weights": os.path.basename(est_path),
+                          "trained_on": est_meta.get("workload"),
+                          "train_seeds": est_meta.get("train_seeds")}}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -461,6 +468,7 @@ def main():
     ap.add_argument("--n", type=int, default=None, help="override the vertex count (profiling cases)")
     ap.add_argument("--ncomp", type=int, default=4096, help="components of batch4096")
     ap.add_argument("--max-iters", type=int, default=30)
+    ap.add_argument("--estimator", default=None, help="estimator weights (.npz) for the batched runs")
     ap.add_argument("--phase-budget-gb", type=float, default=0.0,
                     help="column-batch staging budget for zipf4m (0: one batch)")
     args = ap.parse_args()

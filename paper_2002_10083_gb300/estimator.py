@@ -26,6 +26,8 @@ from . import mcl, synth
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 DEFAULT_WEIGHTS = os.path.join(HERE, "estimator_zipf.npz")
+# weights trained on the batched planted-partition family (256-component batches)
+BATCH_WEIGHTS = os.path.join(HERE, "estimator_batch.npz")
 NH = 64
 SHAPES = [("W1", (NH, mcl.NFEATURES)), ("b1", (NH,)), ("W2", (NH, NH)), ("b2", (NH,)),
           ("W3", (2, NH)), ("b3", (2,))]
@@ -158,8 +160,8 @@ def install(ctx: mcl.Context, path=DEFAULT_WEIGHTS, safety=None):
 
 
 def _gen(args):
-    name, seed = args
-    A = synth.config(name, seed=seed)
+    name, seed, kw = args
+    A = synth.config(name, seed=seed, **kw)
     return synth.CSC(n=A.n, colptr=A.colptr, rowidx=A.rowidx, val=A.val.astype(np.float32))
 
 
@@ -173,6 +175,7 @@ def main():
     ap.add_argument("--epochs", type=int, default=8)
     ap.add_argument("--quantile", type=float, default=0.98)
     ap.add_argument("--procs", type=int, default=8)
+    ap.add_argument("--ncomp", type=int, default=None, help="components of a batch4096 graph")
     ap.add_argument("--out", default=DEFAULT_WEIGHTS)
     args = ap.parse_args()
 
@@ -185,7 +188,8 @@ def main():
     # graphs are generated in worker processes started before any CUDA call
     import multiprocessing as mp
     with mp.get_context("spawn").Pool(args.procs) as pool:
-        graphs = pool.map(_gen, [(args.workload, s) for s in tr + ev])
+        kw = {"ncomp": args.ncomp} if args.ncomp else {}
+        graphs = pool.map(_gen, [(args.workload, s, kw) for s in tr + ev])
     print(f"generated {len(graphs)} graphs in {time.time() - t0:.0f}s", flush=True)
     ctx = mcl.Context(0)
     Xs, Ts = [], []
@@ -206,7 +210,7 @@ def main():
     tr_stats, _ = evaluate(ctx, X, T, wb, norm)
     ev_stats, ratio = evaluate(ctx, Xe, Te, wb, norm)
     safety = max(1.0, float(torch.quantile(ratio.float(), args.quantile).item()))
-    meta = {"workload": args.workload, "train_seeds": tr, "eval_seeds": ev,
+    meta = {"workload": args.workload, "ncomp": args.ncomp, "train_seeds": tr, "eval_seeds": ev,
             "iterations": args.iterations, "samples_per_iteration": args.sample,
             "epochs": args.epochs, "train": tr_stats, "eval": ev_stats, "loss_history": hist,
             "safety_quantile": args.quantile, "safety": safety}
