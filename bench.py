@@ -454,6 +454,51 @@ def run_batched(args):
     return 0
 
 
+def run_planted(args):
+    """The 2,000-vertex planted partition to convergence (K 100): GPU time of
+    mcl_run, and as cpu_baseline the FP64 oracle's whole loop on the host cores."""
+    import torch
+    from paper_2002_10083_gb300 import mcl, synth
+    A = synth.config("planted2k", seed=0)
+    A32 = synth.CSC(n=A.n, colptr=A.colptr, rowidx=A.rowidx, val=A.val.astype(np.float32))
+    D = mcl.DeviceCSC.from_host(A32)
+    ctx = mcl.Context(0)
+    prm = mcl.Params(threshold=1e-4, select_k=100, recover_pct=0.9, inflation=2.0,
+                     chaos_eps=1e-3, max_iters=30)
+    for _ in range(max(args.warmup, 1)):
+        ctx.run(D, prm, keep_final=False)
+    torch.cuda.synchronize()
+    reps = max(args.steps, 1)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        lab, iters, hist, _, nc = ctx.run(D, prm, keep_final=False)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    cpu = None
+    if not args.no_cpu_baseline:
+        import oracle
+        oprm = oracle.Params(theta=float(np.float32(1e-4)), K=100, p=float(np.float32(0.9)),
+                             r=2.0, eps=1e-3, max_iters=30)
+        Ad = synth.CSC(n=A.n, colptr=A.colptr, rowidx=A.rowidx,
+                       val=A.val.astype(np.float32).astype(np.float64))
+        t0 = time.perf_counter()
+        _, o_iters, _, o_lab = oracle.run_mcl(Ad, oprm)
+        dt = time.perf_counter() - t0
+        cpu = {"value": round(o_iters / dt, 4), "unit": "MCL iters/s", "cores": oracle.num_threads(),
+               "kind": "oracle", "sample": f"the whole run ({o_iters} iterations, {dt:.2f} s)"}
+    line = {"metric": METRIC, "workload": "planted2k: 20 clusters x 100 vertices, p_in 0.1, "
+            "p_out 0.001, K 100, theta 1e-4, p 0.9, r 2, to chaos < 1e-3",
+            "n": A.n, "nnz": A.nnz, "iterations": iters, "converged": not nc,
+            "ms_per_run": round(ms, 3), "iters_per_s": round(iters / (ms / 1000.0), 2),
+            "clusters": int(len(np.unique(lab.cpu().numpy()))), "cpu_baseline": cpu}
+    print(json.dumps(line), flush=True)
+    ctx.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -478,6 +523,8 @@ def main():
         return run_reference(args)
     if args.workload in ("batch4096", "zipf4m"):
         return run_batched(args)
+    if args.workload == "planted2k":
+        return run_planted(args)
     return run_gpu(args)
 
 

@@ -448,11 +448,10 @@ static mcl_status expand_impl(mcl_ctx* c, const mcl_csc* A, const mcl_params* pr
                 const int64_t maxf = (int64_t)c->hctr->max_flops;
                 int64_t capb = (int64_t)(c->bucket_budget / ((size_t)g * 8));
                 if (capb > maxf) capb = maxf;
-                if (capb >= 1024 && ensure(c, c->bucket_row, (size_t)g * capb * 4, s) &&
-                    ensure(c, c->bucket_val, (size_t)g * capb * 4, s) &&
+                if (capb >= 1024 && ensure(c, c->bucket_row, (size_t)g * capb * 8, s) &&
                     ensure(c, c->woff, (size_t)g * (WINDOW_MAX + 1) * 4, s)) {
                     bq.bucket_row = (int32_t*)c->bucket_row.p;
-                    bq.bucket_val = (float*)c->bucket_val.p;
+                    bq.bucket_val = nullptr;
                     bq.woff = (int32_t*)c->woff.p;
                     bq.bucket_cap = capb;
                 }
@@ -956,9 +955,9 @@ static void static_iteration(mcl_ctx* c, const mcl_params* prm, const PruneParam
         ExpandBuffers bq = b;
         if (q == NCONF - 1 && c->bucket_row.p) {
             bq.bucket_row = (int32_t*)c->bucket_row.p;
-            bq.bucket_val = (float*)c->bucket_val.p;
+            bq.bucket_val = nullptr;
             bq.woff = (int32_t*)c->woff.p;
-            bq.bucket_cap = (int64_t)(c->bucket_row.bytes / ((size_t)g * 4));
+            bq.bucket_cap = (int64_t)(c->bucket_row.bytes / ((size_t)g * 8));
         }
         launch_numeric(q, Av, pp, bq, g, s);
     }
@@ -1016,11 +1015,10 @@ static mcl_status graph_prepare(mcl_ctx* c, const mcl_params* prm, const PrunePa
         if (!ensure(c, c->cohen_m, n1 * c->cohen_r * 4, s) || !ensure(c, c->cohen_e, n1 * 4, s))
             return fail(c, MCL_ERR_OOM, "estimator scratch allocation failed");
     }
-    if (capb >= 1024 && ensure(c, c->bucket_row, (size_t)g1 * capb * 4, s) &&
-        ensure(c, c->bucket_val, (size_t)g1 * capb * 4, s) &&
+    if (capb >= 1024 && ensure(c, c->bucket_row, (size_t)g1 * capb * 8, s) &&
         ensure(c, c->woff, (size_t)g1 * (WINDOW_MAX + 1) * 4, s)) {
         // exact per-CTA capacity recorded in the buffer sizes
-        c->bucket_row.bytes = (size_t)g1 * capb * 4;
+        c->bucket_row.bytes = (size_t)g1 * capb * 8;
     } else {
         dev_free(c, c->bucket_row.p, s);
         c->bucket_row = Buf{};

@@ -498,8 +498,9 @@ __global__ void __launch_bounds__(T, MINB) k_expand(ExpandArgs a) {
     const ExpandBuffers& b = a.b;
     DevCounters* ctr = b.ctr;
     SrcMeta meta(b.cursors + (int64_t)blockIdx.x * 6 * b.cur_stride, b.cur_stride);
-    int32_t* brow = b.bucket_row ? b.bucket_row + (int64_t)blockIdx.x * b.bucket_cap : nullptr;
-    float* bval = b.bucket_val ? b.bucket_val + (int64_t)blockIdx.x * b.bucket_cap : nullptr;
+    // per-CTA bucket of (row, bits(product)) pairs
+    int2* bkt = b.bucket_row ? reinterpret_cast<int2*>(b.bucket_row) + (int64_t)blockIdx.x * b.bucket_cap
+                             : nullptr;
     int32_t* woff = b.woff ? b.woff + (int64_t)blockIdx.x * (WINDOW_MAX + 1) : nullptr;
     const int wbeg = ctr->bin_off[a.conf * NZ], wend = ctr->bin_off[a.conf * NZ + NZ];
     if (ctr->err & ERR_STAGING) return;  // the iteration is redone without the graph
@@ -558,7 +559,7 @@ __global__ void __launch_bounds__(T, MINB) k_expand(ExpandArgs a) {
         if (nw64 < 1) nw64 = 1;
         if (nw64 > span) nw64 = span;
         bool bucket = false;
-        if (nw64 > 1 && brow != nullptr && flops_j <= b.bucket_cap) {
+        if (nw64 > 1 && bkt != nullptr && flops_j <= b.bucket_cap) {
             const int64_t wmax = WINDOW_MAX < HS ? WINDOW_MAX : HS;
             if (nw64 > wmax) nw64 = wmax;
             bucket = true;
@@ -672,8 +673,7 @@ __global__ void __launch_bounds__(T, MINB) k_expand(ExpandArgs a) {
                         base = __shfl_sync(FULL, base, hl);
                         if (v) {
                             const int pos = base + lane - hl;
-                            brow[pos] = row;
-                            bval[pos] = pv[c] * akj;
+                            bkt[pos] = make_int2(row, __float_as_int(pv[c] * akj));
                         }
                     }
                 }
@@ -750,8 +750,9 @@ __global__ void __launch_bounds__(T, MINB) k_expand(ExpandArgs a) {
 #pragma unroll
                     for (int u = 0; u < 4; ++u) {
                         const int p = pb + 32 * u + lane;
-                        rr[u] = p < be ? brow[p] : -1;
-                        pv[u] = p < be ? bval[p] : 0.0f;
+                        const int2 x = p < be ? bkt[p] : make_int2(-1, 0);
+                        rr[u] = x.x;
+                        pv[u] = __int_as_float(x.y);
                     }
 #pragma unroll
                     for (int u = 0; u < 4; ++u) {
