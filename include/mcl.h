@@ -189,6 +189,12 @@ mcl_status mcl_components(mcl_ctx* ctx, const mcl_csc* A, int32_t* labels, void*
  * final_out: optional; receives the final matrix (allocated as in
  * mcl_expand).  Synchronises `stream` every iteration.  Returns
  * MCL_ERR_NOT_CONVERGED (with all outputs valid) when max_iters is reached.
+ * Batched runs replay every iteration after the first as one CUDA graph on
+ * a stream of the context (MCL_OPT_GRAPH; two replay buffers sized once by
+ * sum_c |c| * min(|c|, K_rec)), ordered after `stream` and before the
+ * labelling.  With prm->use_estimator, an iteration whose learned estimates
+ * fall short on more than 1/20 of its expanded columns hands the rest of the
+ * run to the exact symbolic sizing (mcl_stats.exact_from).
  */
 mcl_status mcl_run(mcl_ctx* ctx, const mcl_csc* A0, const int32_t* comp_offsets, int32_t ncomp,
                    const mcl_params* prm, int32_t* labels, int32_t* iters, double* chaos_hist,
