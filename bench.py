@@ -122,6 +122,20 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def max_over_ranks(ms: float, dist, device: str = "cpu") -> float:
+    """The slowest rank's time (every rank gets it)."""
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_gflops(flops_per_rank: int, ms: float, world: int) -> float:
+    """Whole-job expansion GFLOP/s: every rank runs a replica of the step,
+    so the job does world x flops multiply-adds in the slowest rank's time."""
+    return 2.0 * flops_per_rank * world / (ms / 1000.0) / 1e9
+
+
 def make_workload(name: str, seed: int = 0, n: int | None = None):
     from paper_2002_10083_gb300 import synth
     cache = os.environ.get("MCL_BENCH_CACHE", "/tmp/mcl_bench_cache")
@@ -256,9 +270,7 @@ def run_gpu(args):
         dist.barrier()
     clocks = clk.stop() if clk else None
     if dist:
-        t = torch.tensor([ms], device=f"cuda:{dev}")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+        ms = max_over_ranks(ms, dist, device=f"cuda:{dev}")
     flops = int(st["flops"])
     nnz_out, nnz_b = int(st["nnz_out"]), int(st["nnz_b"])
     # the other form, same workload, for the comparison the metric asks for
@@ -307,8 +319,8 @@ def run_gpu(args):
 
     if rank != 0:
         return 0
-    gflops = 2.0 * flops / (ms / 1000.0) / 1e9 * world
-    e2e_gflops = 2.0 * flops / (e2e_ms / 1000.0) / 1e9 * world if e2e_steps else None
+    gflops = job_gflops(flops, ms, world)
+    e2e_gflops = job_gflops(flops, e2e_ms, world) if e2e_steps else None
     peak, peak_kind = _peaks()
     b_alg = 8 * nnz + 8 * flops + 8 * nnz_out + 16 * n
     achieved = b_alg / (t_num / 1000.0) / 1e9
@@ -321,7 +333,7 @@ def run_gpu(args):
     other_name = "plain" if main_name == "learned" else "learned"
 
     def form_line(msv, tnum, s):
-        return {"value": round(2.0 * flops / (msv / 1000.0) / 1e9 * world, 2), "unit": "GFLOP/s",
+        return {"value": round(job_gflops(flops, msv, world), 2), "unit": "GFLOP/s",
                 "ms_per_step": round(msv, 3), "iters_per_s": round(1000.0 / msv, 4),
                 "numeric_ms": round(tnum, 3), "estimate_ms": round(s["ms_estimate"], 3),
                 "estimator_misses": int(s["estimator_misses"]), "window_cuts": int(s["range_splits"])}
