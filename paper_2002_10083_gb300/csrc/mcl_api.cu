@@ -30,7 +30,7 @@ struct mcl_ctx {
     char err[512] = {0};
     // scratch
     Buf flops, colsum, rlo, rhi, cap, off, est, bucket, work, kept, chaos, bnnz, tmp_row, tmp_val,
-        cursors, scan, ctr, active, bucket_row, bucket_val, woff, comp_off, comp_of_col,
+        cursors, scan, ctr, active, bucket_row, woff, comp_off, comp_of_col,
         comp_bits, comp_active;
     size_t bucket_budget = (size_t)32 << 30;  // bytes of product buckets (large config)
     size_t phase_budget = 0;                  // bytes of output staging per column batch (0: one)
@@ -188,7 +188,6 @@ ExpandBuffers buffers(mcl_ctx* c) {
     b.active = nullptr;
     b.nnz_is_bound = 0;
     b.bucket_row = nullptr;
-    b.bucket_val = nullptr;
     b.woff = nullptr;
     b.bucket_cap = 0;
     return b;
@@ -285,7 +284,7 @@ void mcl_destroy(mcl_ctx* c) {
     if (!c) return;
     cudaSetDevice(c->device);
     cudaDeviceSynchronize();
-    Buf* all[] = {&c->phase_colptr, &c->bucket_row, &c->bucket_val, &c->woff, &c->comp_off,
+    Buf* all[] = {&c->phase_colptr, &c->bucket_row, &c->woff, &c->comp_off,
                   &c->comp_of_col,
                   &c->comp_bits, &c->comp_active,
                   &c->flops, &c->colsum, &c->rlo, &c->rhi,  &c->cap,     &c->off,  &c->est,
@@ -440,7 +439,6 @@ static mcl_status expand_impl(mcl_ctx* c, const mcl_csc* A, const mcl_params* pr
             const int g = numeric_grid(q, pp, c->num_sms);
             ExpandBuffers bq = bb;
             bq.bucket_row = nullptr;
-            bq.bucket_val = nullptr;
             bq.woff = nullptr;
             bq.bucket_cap = 0;
             if (q == NCONF - 1) {
@@ -451,8 +449,7 @@ static mcl_status expand_impl(mcl_ctx* c, const mcl_csc* A, const mcl_params* pr
                 if (capb >= 1024 && ensure(c, c->bucket_row, (size_t)g * capb * 8, s) &&
                     ensure(c, c->woff, (size_t)g * (WINDOW_MAX + 1) * 4, s)) {
                     bq.bucket_row = (int32_t*)c->bucket_row.p;
-                    bq.bucket_val = nullptr;
-                    bq.woff = (int32_t*)c->woff.p;
+                            bq.woff = (int32_t*)c->woff.p;
                     bq.bucket_cap = capb;
                 }
             }
@@ -955,7 +952,6 @@ static void static_iteration(mcl_ctx* c, const mcl_params* prm, const PruneParam
         ExpandBuffers bq = b;
         if (q == NCONF - 1 && c->bucket_row.p) {
             bq.bucket_row = (int32_t*)c->bucket_row.p;
-            bq.bucket_val = nullptr;
             bq.woff = (int32_t*)c->woff.p;
             bq.bucket_cap = (int64_t)(c->bucket_row.bytes / ((size_t)g * 8));
         }

@@ -88,7 +88,6 @@ struct ExpandBuffers {
     int32_t* cursors;   // per CTA: source metadata, 6 * cur_stride int32
     int64_t cur_stride;
     int32_t* bucket_row;   // per CTA: bucket_cap (row, bits(a_ik * a_kj)) pairs (int2)
-    float* bucket_val;     // unused (pairs are interleaved in bucket_row)
     int32_t* woff;         // per CTA: window offsets into the bucket (WINDOW_MAX + 1)
     int64_t bucket_cap;
     int64_t* scan_tmp;  // tile sums

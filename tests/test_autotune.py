@@ -41,3 +41,41 @@ def test_table_round_trip_and_apply(tmp_path):
     assert got == res["best"]
     assert ctx.opts == {autotune.OPT_TABLE: 2, autotune.OPT_PLAN: 1536, autotune.OPT_SMALL_MAX: 256}
     assert autotune.apply(FakeCtx(), back, "NVIDIA GB300", "n1-mean1-max1") is None
+
+
+class _Csc:
+    def __init__(self, colptr, rowidx, val):
+        import torch
+        self.colptr = torch.tensor(colptr, dtype=torch.int64)
+        self.rowidx = torch.tensor(rowidx, dtype=torch.int32)
+        self.val = torch.tensor(val, dtype=torch.float32)
+
+
+def test_same_result_check_tolerates_only_rounding_level_changes():
+    pytest = __import__("pytest")
+    pytest.importorskip("torch")
+    # 2000 columns of 2 entries each
+    n = 2000
+    colptr = [2 * j for j in range(n + 1)]
+    rows = [r for j in range(n) for r in (j, j + 1)]
+    vals = [0.75, 0.25] * n
+    ref = _Csc(colptr, rows, vals)
+    assert autotune._same(_Csc(colptr, rows, vals), ref)
+    # values within 1e-5 relative
+    assert autotune._same(_Csc(colptr, rows, [v * (1 + 5e-6) for v in vals]), ref)
+    assert not autotune._same(_Csc(colptr, rows, [v * (1 + 5e-5) for v in vals]), ref)
+    # one column keeps a tied entry on another row: 1 of 4000 entries
+    rows2 = list(rows)
+    rows2[1] = 7
+    assert autotune._same(_Csc(colptr, rows2, vals), ref)
+    # many rows differ
+    rows3 = [r + 1 for r in rows]
+    assert not autotune._same(_Csc(colptr, rows3, vals), ref)
+    # one column one entry shorter (a tie at the recovery mass): 1 of 2000 columns
+    cp4 = [0] + [2 * j - 1 for j in range(1, n + 1)]
+    rows4 = rows[1:]
+    vals4 = vals[1:]
+    assert autotune._same(_Csc(cp4, rows4, vals4), ref)
+    # many columns shorter
+    cp5 = [j for j in range(n + 1)]
+    assert not autotune._same(_Csc(cp5, rows[:n], vals[:n]), ref)
