@@ -445,3 +445,21 @@ def test_zipf4m_degree_law_column_batched_sampled():
                            np.argsort(-deg)[:20]]).astype(np.int32)
     rep, _ = compare_iteration(A, G, _oprm(prm), cols=cols, rtol=RTOL)
     assert rep.ok(), rep.failures[:5]
+
+
+def test_checkpointed_run_equals_mcl_run(ctx, tmp_path):
+    """A run stopped after 3 iterations and resumed from its checkpoint ends
+    with mcl_run's iterations and clusters."""
+    from paper_2002_10083_gb300 import checkpoint
+    A = synth.config("planted2k", seed=3).with_val32()
+    prm = _prm(theta=1e-4, K=100, p=0.9, iters=30)
+    lab0, it0, hist0, _, nc0 = ctx.run(_dev(A), prm, keep_final=False)
+    path = str(tmp_path / "run.npz")
+    lab1, it1, _, _, _ = checkpoint.run(ctx, A, prm, path, stop_after=3)
+    assert lab1 is None and it1 == 3
+    lab2, it2, hist2, _, conv2 = checkpoint.run(ctx, A, prm, path)
+    assert conv2 == (not nc0) and it2 == it0
+    assert np.array_equal(lab2.cpu().numpy(), lab0.cpu().numpy())
+    # FP32 atomic accumulation orders differ between any two runs and compound
+    # over iterations: chaos (in [0, 1]) agrees to 1e-3
+    np.testing.assert_allclose(hist2, hist0, rtol=0, atol=1e-3)
