@@ -26,7 +26,9 @@
  *   chaos          chaos_j = max(0, max_i a_ij - sum_i a_ij^2) on the
  *                  normalised column; the convergence test of Alg. 1
  *                  ("while change in successive iterations") reads
- *                  max_j chaos_j;
+ *                  max_j chaos_j.  The paper gives no formula: this is a
+ *                  reading, pinned to closed forms (tests/golden/
+ *                  chaos_cases.txt), parity unpinned against the paper;
  *   clusters       connected components of the final matrix's undirected
  *                  pattern (Alg. 1, return), union-find; label = smallest
  *                  vertex id of the component.
