@@ -1127,6 +1127,7 @@ mcl_status mcl_run(mcl_ctx* c, const mcl_csc* A0, const int32_t* comp_offsets, i
                 st = graph_prepare(c, prm, gpp, comp_offsets, ncomp, &cur, gsizing, G, s);
                 if (st) {
                     graph_release(c, G, s, -1);
+                    if (owned) free_csc(c, &cur, s);  // no-op if graph_prepare took it over
                     c->iteration = saved_iter;
                     c->run_exact = 0;
                     return st;
