@@ -406,8 +406,9 @@ def test_batched_graph_replay_matches_eager(ctx, cap, learned, scale):
         assert replays == it1 - 1
     assert np.array_equal(lab0.cpu().numpy(), lab1.cpu().numpy())
     # FP32 atomic accumulation orders differ from run to run, graph or not, and
-    # the matrices of later iterations inherit those last-bit differences
-    np.testing.assert_allclose(hist1[:it1], hist0[:it0], rtol=1e-3, atol=2e-4)
+    # the matrices of later iterations inherit those last-bit differences:
+    # chaos (in [0, 1]) agrees to 1e-3 (3.6e-4 seen at iteration 16)
+    np.testing.assert_allclose(hist1[:it1], hist0[:it0], rtol=0, atol=1e-3)
     # and the per-component oracle
     _, o_iters, _, o_lab = oracle.run_mcl(A, _oprm(prm), per_component=offs)
     assert it1 == max(o_iters)
