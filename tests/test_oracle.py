@@ -7,6 +7,7 @@ mathematics (not against the oracle itself).
   normalisation;
 * the prune rule on hand-derived cases and on special cases that reduce to
   a plain sort / mask / cumulative sum;
+* inflation at r = 0.5 ... 5 on hand-derived columns (tests/golden/inflate_cases.txt);
 * chaos closed forms;
 * planted cliques are an exact fixed point, recovered after one iteration;
 * components == scipy's connected_components; vertex relabelling commutes.
@@ -153,6 +154,47 @@ def test_chaos_golden(golden_dir):
         v = [float(x) for x in vals]
         A = _one_col(list(range(len(v))), v)
         assert abs(oracle.chaos_cols(A)[0] - float(want[0])) < 1e-15
+
+
+def _inflate_cases(golden_dir):
+    out = []
+    for r, vals, want in _read_cases(os.path.join(golden_dir, "inflate_cases.txt")):
+        num = [float(x) for x in want[:-2]]
+        assert want[-2] == "/"
+        out.append((float(r[0]), [float(v) for v in vals], np.array(num) / float(want[-1])))
+    return out
+
+
+def test_inflation_golden_cases(golden_dir):
+    """Inflation at r != 1 against hand-derived columns (a wrong exponent,
+    e.g. 1/r or r - 1, or a skipped power fails here)."""
+    cases = _inflate_cases(golden_dir)
+    assert len(cases) >= 8 and any(r not in (1.0, 2.0) for r, _, _ in cases)
+    for r, vals, want in cases:
+        A = _one_col(list(range(len(vals))), vals)
+        out, ch = oracle.inflate_normalize(A, r)
+        np.testing.assert_allclose(out.val, want, rtol=1e-14, atol=0, err_msg=f"r={r} {vals}")
+        # chaos of the inflated column: max a - sum a^2
+        assert abs(ch[0] - max(0.0, want.max() - (want ** 2).sum())) < 1e-15
+
+
+def test_inflation_golden_cases_through_expansion(golden_dir):
+    """The same columns as the last column of B = A A: columns 0..m-1 of A
+    are unit vectors e_i, column m holds the case's values, so B's column m
+    equals it; theta = 0, K >= m, p = 1 keep every entry, and the iteration
+    returns the inflated, renormalised column."""
+    for r, vals, want in _inflate_cases(golden_dir):
+        m = len(vals)
+        colptr = np.concatenate([np.arange(m + 1), [2 * m]]).astype(np.int64)
+        rowidx = np.concatenate([np.arange(m), np.arange(m)]).astype(np.int32)
+        val = np.concatenate([np.ones(m), vals])
+        A = synth.CSC(n=m + 1, colptr=colptr, rowidx=rowidx, val=val)
+        res = oracle.expand_cols(A, oracle.Params(theta=0.0, K=m + 1, p=1.0, r=r),
+                                 cols=np.array([m], np.int32), inflate=True)
+        assert res.mstar[0] == m and res.bnnz[0] == m
+        assert np.array_equal(res.out_rows[0, :m], np.arange(m))
+        np.testing.assert_allclose(res.out_vals[0, :m], want, rtol=1e-14, atol=0,
+                                   err_msg=f"r={r} {vals}")
 
 
 @pytest.mark.parametrize("seed", range(4))
