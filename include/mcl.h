@@ -344,8 +344,9 @@ mcl_status mcl_get_stats(mcl_ctx* ctx, mcl_stats* stats);
  * stream capture.  Every call shares the one array, which keeps the last
  * call's contents (the call clears what must start at zero): calls that
  * overlap on the GPU -- on different streams or host threads -- race and
- * must be serialised by the caller.  Synchronises `stream` once (after the
- * column statistics, to check them and size the cursors).
+ * must be serialised by the caller.  Synchronises `stream` after the column
+ * statistics (to check them and size the cursors) and, when nnz_out is
+ * given, once more after the counting pass (to read its error flags).
  */
 #define MCL_NOALLOC_SCRATCH_BYTES (64 * 1024 * 1024)
 mcl_status mcl_symbolic_noalloc(const mcl_csc* A, int64_t* flops, int64_t* nnz_out, char* errbuf,

@@ -34,7 +34,7 @@ def nvcc() -> str:
 
 def _flags(verbose_ptxas: bool = False):
     f = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
-                "--use_fast_math" if False else "-prec-div=true", "-I", os.path.join(ROOT, "include"),
+                "-prec-div=true", "-I", os.path.join(ROOT, "include"),
                 "-I", CSRC]
     if verbose_ptxas:
         f += ["-Xptxas", "-v"]

@@ -19,6 +19,7 @@
 #include <cfloat>
 #include <climits>
 #include <cstdint>
+#include <mutex>
 
 #include "mcl_device.cuh"
 #include "mcl_internal.h"
@@ -351,13 +352,28 @@ __global__ void __launch_bounds__(SYM_T) k_symbolic(CscView A, ExpandBuffers b, 
     }
 }
 
+// The dynamic shared-memory limit is a per-device attribute of the kernel:
+// it is set on the current device before every launch, and the occupancy it
+// gives is cached per device (first use under a lock).
+static void symbolic_set_smem() {
+    cudaFuncSetAttribute(k_symbolic, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)(SYM_WORDS * 4 + sizeof(SymShared)));
+}
+
 int symbolic_grid(int num_sms) {
-    static int occ = -1;
-    if (occ < 0) {
-        size_t smem = SYM_WORDS * 4 + sizeof(SymShared);
-        cudaFuncSetAttribute(k_symbolic, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_symbolic, SYM_T, smem);
+    constexpr int kMaxDev = 64;
+    static std::mutex mu;
+    static int occ_dev[kMaxDev] = {0};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lk(mu);
+    int occ = (dev >= 0 && dev < kMaxDev) ? occ_dev[dev] : 0;
+    if (occ < 1) {
+        symbolic_set_smem();
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_symbolic, SYM_T,
+                                                      SYM_WORDS * 4 + sizeof(SymShared));
         if (occ < 1) occ = 1;
+        if (dev >= 0 && dev < kMaxDev) occ_dev[dev] = occ;
     }
     return occ * num_sms;
 }
@@ -366,6 +382,7 @@ void launch_symbolic(const CscView& A, const ExpandBuffers& b, int64_t* nnz_out,
                      int grid_cap, cudaStream_t s) {
     if (A.n == 0) return;
     size_t smem = SYM_WORDS * 4 + sizeof(SymShared);
+    symbolic_set_smem();
     int grid = symbolic_grid(num_sms);
     if (grid > grid_cap) grid = grid_cap;
     if ((int64_t)grid > A.n) grid = (int)A.n;

@@ -137,6 +137,25 @@ extern "C" mcl_status mcl_symbolic_noalloc(const mcl_csc* A, int64_t* flops, int
         if (grid > gmax) grid = gmax;
         b.cursors = reinterpret_cast<int32_t*>(sb + off_cur);
         launch_symbolic(Av, b, nnz_out, num_sms > 0 ? num_sms : 1, grid, s);
+        // the pass flags a column longer than its cursor space (not expected:
+        // the stride exceeds the longest column) instead of writing its count
+        const cudaError_t le = cudaGetLastError();
+        if (le != cudaSuccess) {
+            put_error(errbuf, errlen, "launch failed: %s", cudaGetErrorString(le));
+            return MCL_ERR_CUDA;
+        }
+        err = 0;
+        if (cudaMemcpyAsync(&err, &b.ctr->err, sizeof(err), cudaMemcpyDeviceToHost, s) !=
+                cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess) {
+            const cudaError_t e2 = cudaGetLastError();
+            put_error(errbuf, errlen, "symbolic pass failed: %s", cudaGetErrorString(e2));
+            return MCL_ERR_CUDA;
+        }
+        if (err) {
+            put_error(errbuf, errlen, "symbolic pass raised flags 0x%x", err);
+            return MCL_ERR_INTERNAL;
+        }
     }
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {
