@@ -111,6 +111,8 @@ typedef struct {
     int32_t exact_from;       /* mcl_run with use_estimator: first iteration sized exactly because
                                  the learned estimates of an earlier one fell short on more than
                                  1/20 of its columns (0: none) */
+    int32_t groups;           /* groups of components of the last batched mcl_run
+                                 (MCL_OPT_GROUP_BUDGET; 1 when it ran as one group) */
 } mcl_stats;
 
 /* Create a context on `device` (made current by every call).  alloc/free
@@ -237,6 +239,18 @@ mcl_status mcl_symbolic(mcl_ctx* ctx, const mcl_csc* A, int64_t* flops, int64_t*
  *                        sum over components of size * min(size, K_rec), an
  *                        upper bound on any later iteration.  An iteration
  *                        that would exceed it is redone without graphs.
+ *  11 MCL_OPT_SMALL_MAX  columns estimated at <= value entries (0..512,
+ *                        default 512) use the small numeric configuration
+ *  12 MCL_OPT_TABLE      shape of the large numeric configuration (0..2)
+ *  13 MCL_OPT_PLAN       entries planned per hashed window (0 = half the
+ *                        table, at most 3072)
+ *  14 MCL_OPT_GROUP_BUDGET  bytes of device memory one group of components
+ *                        may use in a batched mcl_run; 0 (default) = one
+ *                        group.  A batch whose components need more (about
+ *                        32 bytes per entry of size * min(size, K_rec) plus
+ *                        160 bytes per vertex) runs in consecutive groups of
+ *                        whole components, each to its own convergence, with
+ *                        the same results as one run.
  * Returns MCL_ERR_INVALID for an unknown option or value.
  */
 #define MCL_OPT_SIZING 1
@@ -249,6 +263,10 @@ mcl_status mcl_symbolic(mcl_ctx* ctx, const mcl_csc* A, int64_t* flops, int64_t*
 #define MCL_OPT_COHEN_SEED 8
 #define MCL_OPT_GRAPH 9
 #define MCL_OPT_GRAPH_CAP 10
+#define MCL_OPT_SMALL_MAX 11
+#define MCL_OPT_TABLE 12
+#define MCL_OPT_PLAN 13
+#define MCL_OPT_GROUP_BUDGET 14
 mcl_status mcl_set_option(mcl_ctx* ctx, int option, int64_t value);
 
 /*

@@ -30,8 +30,8 @@ struct mcl_ctx {
     char err[512] = {0};
     // scratch
     Buf flops, colsum, rlo, rhi, cap, off, est, bucket, work, kept, chaos, bnnz, tmp_row, tmp_val,
-        cursors, scan, ctr, active, bucket_row, woff, comp_off, comp_of_col,
-        comp_bits, comp_active;
+        cursors, scan, ctr, active, bucket_row, woff, comp_off, comp_of_col, comp_bits,
+        comp_active;
     size_t bucket_budget = (size_t)32 << 30;  // bytes of product buckets (large config)
     size_t phase_budget = 0;                  // bytes of output staging per column batch (0: one)
     Buf phase_colptr;
@@ -49,6 +49,8 @@ struct mcl_ctx {
     int table = 0;          // autotuned: shape of the large configuration
     int plan = 0;           // autotuned: rows planned per window (0: half the table)
     int64_t graph_cap = 0;  // entries of the replay buffers (0: per-component bound)
+    size_t group_budget = 0;  // bytes per group of components in a batched mcl_run (0: one group)
+    int in_group = 0;         // mcl_run is running one group
     // learned estimator (weights on device)
     Buf mlp_w, mlp_norm, colmax, feats, prev_logcf, iter_dev;
     int has_estimator = 0;
@@ -183,13 +185,13 @@ ExpandBuffers buffers(mcl_ctx* c) {
     b.tmp_val = (float*)c->tmp_val.p;
     b.cursors = (int32_t*)c->cursors.p;
     b.cur_stride = 0;
+    b.bucket_row = nullptr;
+    b.woff = nullptr;
+    b.bucket_cap = 0;
     b.scan_tmp = (int64_t*)c->scan.p;
     b.ctr = (DevCounters*)c->ctr.p;
     b.active = nullptr;
     b.nnz_is_bound = 0;
-    b.bucket_row = nullptr;
-    b.woff = nullptr;
-    b.bucket_cap = 0;
     return b;
 }
 
@@ -344,9 +346,13 @@ mcl_status mcl_set_option(mcl_ctx* c, int option, int64_t value) {
             if (value < 0 || value > 2) return fail(c, MCL_ERR_INVALID, "table shape in [0, 2]");
             c->table = (int)value;
             return MCL_OK;
-        case 13:  // rows planned per window of the large configuration (0: half the table)
+        case 13:  // entries planned per hashed window of the large configuration (0: half the table)
             if (value < 0 || value > 3072) return fail(c, MCL_ERR_INVALID, "plan in [0, 3072]");
             c->plan = (int)value;
+            return MCL_OK;
+        case 14:  // device bytes one group of components may use in a batched mcl_run
+            if (value < 0) return fail(c, MCL_ERR_INVALID, "bad group budget");
+            c->group_budget = (size_t)value;
             return MCL_OK;
         case 8:  // seed of Cohen's keys
             c->cohen_seed = (uint64_t)value;
@@ -443,13 +449,14 @@ static mcl_status expand_impl(mcl_ctx* c, const mcl_csc* A, const mcl_params* pr
             bq.bucket_cap = 0;
             if (q == NCONF - 1) {
                 // product buckets for multi-window columns of the large configuration
+                // (optional: without them the windows walk per-source cursors)
                 const int64_t maxf = (int64_t)c->hctr->max_flops;
                 int64_t capb = (int64_t)(c->bucket_budget / ((size_t)g * 8));
                 if (capb > maxf) capb = maxf;
                 if (capb >= 1024 && ensure(c, c->bucket_row, (size_t)g * capb * 8, s) &&
                     ensure(c, c->woff, (size_t)g * (WINDOW_MAX + 1) * 4, s)) {
                     bq.bucket_row = (int32_t*)c->bucket_row.p;
-                            bq.woff = (int32_t*)c->woff.p;
+                    bq.woff = (int32_t*)c->woff.p;
                     bq.bucket_cap = capb;
                 }
             }
@@ -1055,6 +1062,114 @@ static mcl_status graph_prepare(mcl_ctx* c, const mcl_params* prm, const PrunePa
     return MCL_OK;
 }
 
+// Device bytes a batched run of one component of `size` vertices may need:
+// the two graph replay buffers and the output staging (8 bytes per entry of
+// size * min(size, K_rec) each), the first iteration's output, and the
+// per-column scratch.
+static int64_t group_cost(int64_t size, int32_t krec) {
+    return 32 * size * (size < krec ? size : krec) + 160 * size;
+}
+
+// A batched run split into consecutive groups of whole components whose
+// costs fit the group budget: each group is copied out as a matrix of its
+// own (rows re-based), run to its own convergence by mcl_run, and its labels
+// (and final block) are placed back.  The components are independent, so
+// the result is the one of a single run.
+static mcl_status run_groups(mcl_ctx* c, const mcl_csc* A0, const int32_t* offs,
+                             const std::vector<int32_t>& gcut, const mcl_params* prm,
+                             int32_t* labels, int32_t* iters, double* chaos_hist,
+                             mcl_csc* final_out, cudaStream_t s) {
+    const int ngroups = (int)gcut.size() - 1;
+    std::vector<double> hist_g((size_t)prm->max_iters, 0.0);
+    if (chaos_hist)
+        for (int i = 0; i < prm->max_iters; ++i) chaos_hist[i] = 0.0;
+    struct Part {
+        int32_t lo, ng;
+        mcl_csc fin;
+    };
+    std::vector<Part> parts;
+    auto free_parts = [&]() {
+        for (auto& p : parts) free_csc(c, &p.fin, s);
+        parts.clear();
+    };
+    int it_max = 0, replays = 0;
+    bool converged = true;
+    mcl_status st = MCL_OK;
+    for (int g = 0; g < ngroups; ++g) {
+        const int32_t c0 = gcut[g], c1 = gcut[g + 1];
+        const int32_t lo = offs[c0], hi = offs[c1], ng = hi - lo;
+        int64_t pp[2] = {0, 0};
+        CUDA_TRY(c, cudaMemcpyAsync(&pp[0], A0->colptr + lo, 8, cudaMemcpyDeviceToHost, s));
+        CUDA_TRY(c, cudaMemcpyAsync(&pp[1], A0->colptr + hi, 8, cudaMemcpyDeviceToHost, s));
+        CUDA_TRY(c, cudaStreamSynchronize(s));
+        mcl_csc sub{ng, pp[1] - pp[0], nullptr, nullptr, A0->val ? A0->val + pp[0] : nullptr};
+        sub.colptr = (int64_t*)dev_alloc(c, ((size_t)ng + 1) * 8, s);
+        sub.rowidx = (int32_t*)dev_alloc(c, (size_t)sub.nnz * 4 + 4, s);
+        if (!sub.colptr || !sub.rowidx) {
+            dev_free(c, sub.colptr, s);
+            dev_free(c, sub.rowidx, s);
+            free_parts();
+            return fail(c, MCL_ERR_OOM, "group %d of %d: copy allocation failed", g, ngroups);
+        }
+        launch_block_colptr(A0->colptr, lo, ng, sub.colptr, s);
+        launch_add_i32(A0->rowidx + pp[0], sub.nnz, -lo, sub.rowidx, s);
+        std::vector<int32_t> offs_g((size_t)(c1 - c0) + 1);
+        for (int32_t q = c0; q <= c1; ++q) offs_g[q - c0] = offs[q] - lo;
+        int32_t it_g = 0;
+        Part part{lo, ng, mcl_csc{}};
+        c->in_group = 1;
+        st = mcl_run(c, &sub, offs_g.data(), c1 - c0, prm, labels + lo, &it_g, hist_g.data(),
+                     final_out ? &part.fin : nullptr, (void*)s);
+        c->in_group = 0;
+        dev_free(c, sub.colptr, s);
+        dev_free(c, sub.rowidx, s);
+        if (st != MCL_OK && st != MCL_ERR_NOT_CONVERGED) {
+            free_parts();
+            return st;
+        }
+        if (st == MCL_ERR_NOT_CONVERGED) converged = false;
+        launch_add_i32(labels + lo, ng, lo, labels + lo, s);  // group-local labels -> global
+        it_max = it_g > it_max ? it_g : it_max;
+        if (chaos_hist)
+            for (int i = 0; i < it_g; ++i) chaos_hist[i] = hist_g[i] > chaos_hist[i] ? hist_g[i] : chaos_hist[i];
+        replays += c->stats.graph_replays;
+        if (final_out) parts.push_back(part);
+    }
+    if (final_out) {
+        int64_t total = 0;
+        for (auto& p : parts) total += p.fin.nnz;
+        mcl_csc F{A0->n, total, nullptr, nullptr, nullptr};
+        F.colptr = (int64_t*)dev_alloc(c, ((size_t)A0->n + 1) * 8, s);
+        F.rowidx = (int32_t*)dev_alloc(c, (size_t)total * 4 + 4, s);
+        F.val = (float*)dev_alloc(c, (size_t)total * 4 + 4, s);
+        if (!F.colptr || !F.rowidx || !F.val) {
+            free_csc(c, &F, s);
+            free_parts();
+            return fail(c, MCL_ERR_OOM, "final matrix allocation failed");
+        }
+        int64_t base = 0;
+        for (size_t q = 0; q < parts.size(); ++q) {
+            const Part& p = parts[q];
+            launch_place_colptr(p.fin.colptr, p.lo, p.ng, base, q + 1 == parts.size(), F.colptr, s);
+            launch_add_i32(p.fin.rowidx, p.fin.nnz, p.lo, F.rowidx + base, s);
+            if (p.fin.nnz > 0)
+                CUDA_TRY(c, cudaMemcpyAsync(F.val + base, p.fin.val, (size_t)p.fin.nnz * 4,
+                                            cudaMemcpyDeviceToDevice, s));
+            base += p.fin.nnz;
+        }
+        if (parts.empty()) launch_fill_colptr(A0->n, F.colptr, s);
+        free_parts();
+        *final_out = F;
+    }
+    if ((st = check_launch(c, "group placement"))) return st;
+    c->stats.iterations = it_max;
+    c->stats.graph_replays = replays;
+    c->stats.groups = ngroups;
+    if (iters) *iters = it_max;
+    if (!converged) return fail(c, MCL_ERR_NOT_CONVERGED, "max_iters reached in a group");
+    return MCL_OK;
+}
+
 mcl_status mcl_run(mcl_ctx* c, const mcl_csc* A0, const int32_t* comp_offsets, int32_t ncomp,
                    const mcl_params* prm, int32_t* labels, int32_t* iters, double* chaos_hist,
                    mcl_csc* final_out, void* stream) {
@@ -1073,6 +1188,27 @@ mcl_status mcl_run(mcl_ctx* c, const mcl_csc* A0, const int32_t* comp_offsets, i
             if (comp_offsets[q + 1] < comp_offsets[q])
                 return fail(c, MCL_ERR_INVALID, "comp_offsets must be nondecreasing");
         CUDA_TRY(c, cudaSetDevice(c->device));
+        c->stats.groups = 1;
+        if (c->group_budget > 0 && !c->in_group) {
+            // consecutive groups of whole components within the budget
+            PruneParams gp;
+            mcl_status pst = check_params(c, prm, &gp, true);
+            if (pst) return pst;
+            std::vector<int32_t> gcut{0};
+            int64_t used = 0;
+            for (int q = 0; q < ncomp; ++q) {
+                const int64_t cost = group_cost(comp_offsets[q + 1] - comp_offsets[q], gp.Krec);
+                if (q > gcut.back() && used + cost > (int64_t)c->group_budget) {
+                    gcut.push_back(q);
+                    used = 0;
+                }
+                used += cost;
+            }
+            gcut.push_back(ncomp);
+            if (gcut.size() > 2)
+                return run_groups(c, A0, comp_offsets, gcut, prm, labels, iters, chaos_hist,
+                                  final_out, s);
+        }
         const size_t n1 = (size_t)A0->n + 1;
         if (!ensure(c, c->comp_off, (size_t)(ncomp + 1) * 4, s) ||
             !ensure(c, c->comp_of_col, n1 * 4, s) || !ensure(c, c->comp_bits, (size_t)ncomp * 8, s) ||

@@ -124,8 +124,10 @@ __device__ __forceinline__ uint64_t cat_at(const uint64_t* A, int na, const uint
 // #{x : x >= kappa} == M exactly (1 <= M <= na + nb).  Most-significant
 // byte first; stops as soon as the chosen bucket holds exactly the keys
 // still needed, returning its prefix with zero low bits.  Histogram updates
-// are aggregated per warp over lanes with the same digit.
-template <int T>
+// are aggregated per warp over lanes with the same digit.  With SKIP0, zero
+// elements are not keys (empty slots of a table; every key is >= 1) and M
+// counts nonzero keys only.
+template <int T, bool SKIP0 = false>
 __device__ uint64_t block_select_count(const uint64_t* A, int na, const uint64_t* B, int nb, int M,
                                        unsigned* hist, BlockScratch* bs) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -140,7 +142,7 @@ __device__ uint64_t block_select_count(const uint64_t* A, int na, const uint64_t
             const int i = base + tid;
             const bool valid = i < tot;
             const uint64_t x = valid ? cat_at(A, na, B, i) : 0ull;
-            const bool in = valid && (x & hmask) == prefix;
+            const bool in = valid && (!SKIP0 || x != 0ull) && (x & hmask) == prefix;
             const unsigned act = __ballot_sync(FULL, in);
             if (in) {
                 const unsigned dg = (unsigned)((x >> shift) & 255u);

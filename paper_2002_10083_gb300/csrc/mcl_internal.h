@@ -63,7 +63,8 @@ struct PruneParams {
     float r;
     int32_t inflate;
     // tuning (autotuner): columns estimated at <= small_max entries use the
-    // small configuration; shape of the large one; rows planned per window
+    // small configuration; shape of the large one; entries planned per
+    // hashed window
     int32_t small_max;
     int32_t table;
     int32_t plan;
@@ -147,6 +148,11 @@ void launch_comp_chaos(int32_t n, const int32_t* comp_of_col, const uint8_t* act
 void launch_comp_retire(int32_t ncomp, const unsigned long long* comp_bits, double eps,
                         uint8_t* comp_active, DevCounters* ctr, cudaStream_t s);
 void launch_staging_guard(DevCounters* ctr, int64_t capacity, cudaStream_t s);
+void launch_block_colptr(const int64_t* colptr, int32_t lo, int32_t ng, int64_t* colptr_g,
+                         cudaStream_t s);
+void launch_add_i32(const int32_t* src, int64_t m, int32_t delta, int32_t* dst, cudaStream_t s);
+void launch_place_colptr(const int64_t* colptr_g, int32_t lo, int32_t ng, int64_t base, int last,
+                         int64_t* colptr, cudaStream_t s);
 
 // --- estimator (mcl_estimator.cu) ---
 void launch_colmax_features(const CscView& A, int32_t iteration, const float* prev_logcf,

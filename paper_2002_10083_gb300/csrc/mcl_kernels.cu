@@ -840,6 +840,57 @@ void launch_staging_guard(DevCounters* ctr, int64_t capacity, cudaStream_t s) {
     count_launches(1);
 }
 
+// ---------------------------------------------------------------------------
+// groups of components: the diagonal block [lo, hi) of a block-diagonal CSC
+// as a matrix of its own (rows re-based), and the way back
+// ---------------------------------------------------------------------------
+
+// colptr_g[i] = colptr[lo + i] - colptr[lo] for i in [0, ng]
+__global__ void k_block_colptr(const int64_t* colptr, int32_t lo, int32_t ng, int64_t* colptr_g) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i <= ng) colptr_g[i] = colptr[lo + i] - colptr[lo];
+}
+
+// dst[p] = src[p] + delta for p in [0, m)
+__global__ void k_add_i32(const int32_t* src, int64_t m, int32_t delta, int32_t* dst) {
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < m;
+         p += (int64_t)gridDim.x * blockDim.x)
+        dst[p] = src[p] + delta;
+}
+
+// colptr[lo + i] = colptr_g[i] + base for i in [0, ng) (and colptr[lo + ng]
+// when last)
+__global__ void k_place_colptr(const int64_t* colptr_g, int32_t lo, int32_t ng, int64_t base,
+                               int last, int64_t* colptr) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < ng || (last && i == ng)) colptr[lo + i] = colptr_g[i] + base;
+}
+
+static unsigned grid_for(int64_t m) {
+    int64_t b = (m + 255) / 256;
+    if (b < 1) b = 1;
+    if (b > 152 * 32) b = 152 * 32;
+    return (unsigned)b;
+}
+
+void launch_block_colptr(const int64_t* colptr, int32_t lo, int32_t ng, int64_t* colptr_g,
+                         cudaStream_t s) {
+    k_block_colptr<<<grid_for((int64_t)ng + 1), 256, 0, s>>>(colptr, lo, ng, colptr_g);
+    count_launches(1);
+}
+
+void launch_add_i32(const int32_t* src, int64_t m, int32_t delta, int32_t* dst, cudaStream_t s) {
+    if (m <= 0) return;
+    k_add_i32<<<grid_for(m), 256, 0, s>>>(src, m, delta, dst);
+    count_launches(1);
+}
+
+void launch_place_colptr(const int64_t* colptr_g, int32_t lo, int32_t ng, int64_t base, int last,
+                         int64_t* colptr, cudaStream_t s) {
+    k_place_colptr<<<grid_for((int64_t)ng + 1), 256, 0, s>>>(colptr_g, lo, ng, base, last, colptr);
+    count_launches(1);
+}
+
 __global__ void k_fill_colptr(int32_t n, int64_t* colptr) {
     int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (j <= n) colptr[j] = 0;

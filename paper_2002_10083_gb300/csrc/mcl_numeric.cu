@@ -1,29 +1,42 @@
 // The fused numeric pass of one MCL iteration (Algorithm 1: expansion,
-// Prune, inflation) with a shared-memory hash accumulator.
+// Prune, inflation) with a shared-memory accumulator of exact fixed-point
+// sums.
 //
-// One CTA owns one output column j at a time (persistent grid, LPT order).
+// One CTA owns one output column j at a time (persistent grid, work list in
+// longest-first order).  Products a_ik * a_kj are formed in FP32 and added
+// as 64-bit integers: each product is scaled by 2^f_j, where 2^(62 - f_j)
+// bounds the column sum s_j = sum_k a_kj colsum_k(A) (known before any
+// product and bounding every product and every entry, all values being
+// >= 0), and truncated.  Integer addition is associative, so an entry of
+// B_*j does not depend on the order of its additions, on the window plan or
+// on the CTA shape: runs are bit-identical.  The sum is exact up to the
+// truncation of each product (below 2^-62 s_j), far below FP32 resolution
+// for any entry that can survive the prune.
+//
 // The column's row span is cut into row windows sized from the output-size
-// estimate so that each holds about PLAN distinct rows (a table load near
-// 1/2):
+// estimate (about PLAN entries each; windows of at most HS rows give every
+// row its own slot, no hashing):
 //
-//   1. insert:  every product a_ik * a_kj of the window is added into an
-//               open-addressing table (HS slots, row keys claimed by
-//               compare-and-swap, FP32 values, linear probing), so the work
-//               is proportional to the products, not to the row span;
-//   2. extract: over the table, exact column statistics (count, count and
-//               mass above the threshold) and the ranking keys above the
-//               running top-k bound tau, appended to a candidate buffer that
-//               is cut back to the top ksel keys (radix select) when full;
+//   1. insert:  every product of the window is added into its slot: row - r0
+//               in a window of at most HS rows, else linear probing from a
+//               multiplicative hash (int32 row keys claimed by
+//               compare-and-swap, uint64 sums added with integer atomics);
+//   2. extract: over the table, the ranking key (FP32 value bits, row) of
+//               every entry replaces its sum in place, with the exact column
+//               statistics (count, count and mass at or above the
+//               threshold); the keys above the running top-k bound tau go to
+//               a candidate buffer that is cut back to the top ksel keys
+//               (radix select) when full;
 //   3. clear:   the table.
 //
 // Windows come from per-window product buckets (a counting pass and a
-// scatter of (row, product) into window order) or, without bucket space,
-// from per-source cursors over the sorted rows.  A window whose probe runs
-// exceed PMAX slots is split by rows and redone (counted as a split), and
-// the rest of the column starts at the width that fitted; results never
-// depend on the size estimate.  Finally the prune rule picks m* (threshold /
-// top-k / recovery), the kept keys are sorted by row, inflated, renormalised
-// with an FP64 sum and written with chaos_j.
+// scatter of (row, FP32 product) into window order) or, without bucket
+// space, from per-source cursors over the sorted rows.  A hashed window whose
+// probe runs exceed PMAX slots is split by rows and redone (counted as a
+// split), and the rest of the column starts at the width that fitted;
+// results never depend on the size estimate.  Finally the prune rule picks
+// m* (threshold / top-k / recovery), the kept keys are sorted by row,
+// inflated, renormalised with an FP64 sum and written with chaos_j.
 #include <cfloat>
 #include <climits>
 #include <cstdint>
@@ -46,7 +59,25 @@ struct WinShared {
     int ovf2[2];   // the window exceeded its table
     int went2[2];  // entries of the window's table
     int next2[2];  // source counter of the warp-per-source insert
+    double red;    // result of an ordered sum
 };
+
+// Sum of f(s[i]) over i < m in an order that does not depend on the block
+// size: warp 0 alone, lane l taking i = l, l + 32, ..., then a fixed
+// butterfly; the result is broadcast to the block.  Two barriers.
+template <class F>
+__device__ __forceinline__ double ordered_sum(const uint64_t* s, int m, F f, double* slot) {
+    if (threadIdx.x < 32) {
+        double x = 0.0;
+        for (int i = threadIdx.x; i < m; i += 32) x += f(s[i]);
+        x = warp_sum(x);
+        if (threadIdx.x == 0) *slot = x;
+    }
+    __syncthreads();
+    const double r = *slot;
+    __syncthreads();
+    return r;
+}
 
 // Exclusive block scan of one int per thread; *total gets the sum.  Three
 // barriers (the last protects the scratch for the next call).
@@ -212,6 +243,37 @@ __device__ void block_radix_sort_hi(uint64_t* s, uint64_t* tmp, int n, int bits,
     }
 }
 
+// Value mass of the keys >= cut in a[0..n), as an exact integer sum of the
+// values in fixed point (each truncated at 2^-50 of the largest value), so
+// that it does not depend on the order of a's elements.  Warp 0 sums; the
+// result is broadcast to the block.
+template <int T>
+__device__ double mass_at_or_above(const uint64_t* a, int n, uint64_t cut, WinShared* sh) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint64_t kmax = 0;
+    for (int i = threadIdx.x; i < n; i += T) kmax = a[i] > kmax ? a[i] : kmax;
+    kmax = warp_max(kmax);
+    if (lane == 0) sh->bs.q[3][warp] = (long long)kmax;
+    __syncthreads();
+    if (warp == 0) {
+        uint64_t y = lane < T / 32 ? (uint64_t)sh->bs.q[3][lane] : 0ull;
+        y = warp_max(y);
+        const float maxv = key_val(y);
+        int e = 0;
+        frexpf(maxv > 0.0f ? maxv : 1.0f, &e);  // every value < 2^e
+        const int s50 = 50 - e;
+        unsigned long long acc = 0;
+        for (int i = lane; i < n; i += 32)
+            if (a[i] >= cut) acc += __float2ull_rz(ldexpf(key_val(a[i]), s50));
+        acc = warp_sum(acc);
+        if (lane == 0) sh->red = ldexp((double)acc, -s50);
+    }
+    __syncthreads();
+    const double r = sh->red;
+    __syncthreads();
+    return r;
+}
+
 // Finish a column: prune rule on the candidate keys top[0..ntop) plus exact
 // statistics, then the kept keys in row order (sorted here unless the
 // buffer is already row-ordered) written with inflation (pp.inflate) or
@@ -238,15 +300,7 @@ __device__ void finish_column(uint64_t* top, int ntop, int topcap, const PrunePa
         mq = MT;
     } else {
         kq = block_select_count<T>(top, ntop, top, 0, pp.K, hist, &sh->bs);
-        double part = 0.0;
-        for (int i = tid; i < ntop; i += T) {
-            const uint64_t x = top[i];
-            if (x >= kq) part += (double)key_val(x);
-        }
-        double dv[1] = {part};
-        long long qv[1] = {0};
-        block_sum<T>(dv, 1, qv, 0, &sh->bs);
-        mq = dv[0];
+        mq = mass_at_or_above<T>(top, ntop, kq, sh);
     }
     int mstar;
     uint64_t cut;
@@ -313,15 +367,11 @@ __device__ void finish_column(uint64_t* top, int ntop, int topcap, const PrunePa
         }
         __syncthreads();
     }
-    double usum = 0.0;
-    if (pp.inflate)
-        for (int i = tid; i < m; i += T) usum += (double)inflate_value(key_val(top[i]), pp.r);
-    double dv[1] = {usum};
-    long long qv[1] = {0};
-    block_sum<T>(dv, 1, qv, 0, &sh->bs);
-    const double U = dv[0];
+    const float rr = pp.r;
+    const double U = pp.inflate ? ordered_sum(top, m, [rr](uint64_t x) {
+        return (double)inflate_value(key_val(x), rr); }, &sh->red) : 0.0;
     const double invU = U > 0.0 ? 1.0 / U : 0.0;
-    double amax = 0.0, asq = 0.0;
+    double amax = 0.0;
     for (int i = tid; i < m; i += T) {
         const uint64_t x = top[i];
         const float v = key_val(x);
@@ -330,7 +380,6 @@ __device__ void finish_column(uint64_t* top, int ntop, int topcap, const PrunePa
             const double a = (double)inflate_value(v, pp.r) * invU;
             outv = (float)a;
             amax = a > amax ? a : amax;
-            asq += a * a;
         }
         out_row[i] = key_row(x);
         out_val[i] = outv;
@@ -338,9 +387,10 @@ __device__ void finish_column(uint64_t* top, int ntop, int topcap, const PrunePa
     double ch = 0.0;
     if (pp.inflate) {
         const double mx = block_max_d<T>(amax, &sh->bs);
-        double dv2[1] = {asq};
-        block_sum<T>(dv2, 1, qv, 0, &sh->bs);
-        ch = mx - dv2[0];
+        const double sq = ordered_sum(top, m, [rr, invU](uint64_t x) {
+            const double a = (double)inflate_value(key_val(x), rr) * invU;
+            return a * a; }, &sh->red);
+        ch = mx - sq;
         if (ch < 0.0) ch = 0.0;
     }
     if (tid == 0) {
@@ -373,90 +423,53 @@ __device__ __forceinline__ void append_candidates(Enum& en, uint64_t* top, int t
     __syncthreads();
 }
 
-// Table slot: (bits(value) << 32) | row; empty = row -1, value +0.
-constexpr unsigned long long SLOT_EMPTY = 0x00000000FFFFFFFFull;
 
-__device__ __forceinline__ int slot_row(uint64_t x) { return (int)(uint32_t)x; }
-__device__ __forceinline__ float slot_val(uint64_t x) { return __uint_as_float((uint32_t)(x >> 32)); }
-// ranking key (value descending, row ascending) of an occupied slot
-__device__ __forceinline__ uint64_t slot_key(uint64_t x) {
-    return (x & 0xFFFFFFFF00000000ull) | (uint32_t)(0x7FFFFFFF - slot_row(x));
+// ---------------------------------------------------------------------------
+// the accumulator: int32 row keys and uint64 fixed-point sums per slot
+// ---------------------------------------------------------------------------
+
+constexpr int KEY_EMPTY = -1;
+constexpr int PMAX = 64;  // probe run that marks a hashed window as overflowed
+
+__device__ __forceinline__ void red_add_u64(unsigned long long* p, unsigned long long v) {
+    asm volatile("red.shared.add.u64 [%0], %1;" ::"r"((unsigned)__cvta_generic_to_shared(p)), "l"(v)
+                 : "memory");
 }
 
-// The entries of a window's table (thread t takes slots t, t + T, ...).
-template <int T, int HS>
-struct TableEnum {
-    const uint64_t* tab;
-    __device__ int count(uint64_t tau) const {
-        int c = 0;
-        for (int h = threadIdx.x; h < HS; h += T) {
-            const uint64_t x = tab[h];
-            if (x != SLOT_EMPTY) c += slot_key(x) > tau;
-        }
-        return c;
-    }
-    __device__ void emit(uint64_t tau, uint64_t* dst, int base) const {
-        for (int h = threadIdx.x; h < HS; h += T) {
-            const uint64_t x = tab[h];
-            if (x != SLOT_EMPTY) {
-                const uint64_t k = slot_key(x);
-                if (k > tau) dst[base++] = k;
-            }
-        }
-    }
-};
-
-// Add product v at row into the window's table: linear probing from a
-// multiplicative hash; an empty slot is claimed with one 64-bit
-// compare-and-swap that stores the row and the first value together, and a
-// slot that already holds the row gets v added to its value half.  A probe
-// run longer than PMAX slots marks the window as overflowed (its products
-// are then redone in halves); nothing is added in that case.
-template <int HS>
-__device__ __forceinline__ int table_home(int row) {
-    constexpr int LOGHS = HS == 1024 ? 10 : HS == 2048 ? 11 : HS == 4096 ? 12 : HS == 8192 ? 13 : 0;
-    static_assert(LOGHS > 0, "table size");
-    return (int)(((uint32_t)row * 0x9E3779B1u) >> (32 - LOGHS));
+__device__ __forceinline__ int cas_shared(int* p, int cmp, int val) {
+    int old;
+    asm volatile("atom.shared.cas.b32 %0, [%1], %2, %3;"
+                 : "=r"(old)
+                 : "r"((unsigned)__cvta_generic_to_shared(p)), "r"(cmp), "r"(val)
+                 : "memory");
+    return old;
 }
 
-template <int HS>
-__device__ __forceinline__ void table_add(int row, float v, uint64_t* tab, int* ovf) {
-    constexpr int PMAX = 64;
-    int h = table_home<HS>(row);
-    const unsigned long long mine =
-        ((unsigned long long)__float_as_uint(v) << 32) | (unsigned long long)(uint32_t)row;
-    for (int probes = 0;; ++probes) {
-        const unsigned long long old =
-            atomicCAS(reinterpret_cast<unsigned long long*>(tab + h), SLOT_EMPTY, mine);
-        if (old == SLOT_EMPTY) return;
-        if (slot_row(old) == row) {
-            atomicAdd(reinterpret_cast<float*>(tab + h) + 1, v);
-            return;
-        }
-        if (probes >= PMAX) {
-            *ovf = 1;
-            return;
-        }
-        h = (h + 1) & (HS - 1);
+// Fixed-point scale of a column: q = trunc(v * 2^f) with 2^f = sc1 * sc2
+// (two exact power-of-two factors, each representable in FP32).
+struct FixScale {
+    float sc1, sc2, is1, is2;
+    int f;
+    __device__ static float pow2(int e) { return __int_as_float((e + 127) << 23); }
+    __device__ void init(double s) {
+        int e = 0;
+        frexp(s > 0.0 ? s * (1.0 + 1.0 / 1048576.0) : 1.0, &e);  // s (with margin) < 2^e
+        f = 62 - e;
+        const int f1 = max(-126, min(127, f)), f2 = max(-126, min(127, f - f1));
+        sc1 = pow2(f1);
+        sc2 = pow2(f2);
+        is1 = pow2(-f1);
+        is2 = pow2(-f2);
     }
-}
-
-// Expected entries per source and window below which a window walks its
-// sources one per lane instead of one per warp.
-constexpr int LANE_MODE_MAX = 12;
-
-struct ExpandArgs {
-    CscView A;
-    PruneParams pp;
-    ExpandBuffers b;
-    int conf;
-    int plan;
-};
-
-template <int T, int HS>
-struct ExpandLayout {
-    static constexpr size_t bytes(int ksel) {
-        return (size_t)HS * 8 + (size_t)(ksel + HS) * 8 + 256 * 4 + 256 * 8 + sizeof(WinShared);
+    __device__ __forceinline__ unsigned long long q(float aik, float akj) const {
+        const float v = __fmul_rn(aik, akj);  // the FP32 product
+        return __float2ull_rz(__fmul_rn(__fmul_rn(v, sc1), sc2));
+    }
+    __device__ __forceinline__ unsigned long long qv(float v) const {  // v: an FP32 product
+        return __float2ull_rz(__fmul_rn(__fmul_rn(v, sc1), sc2));
+    }
+    __device__ __forceinline__ float value(unsigned long long x) const {
+        return __fmul_rn(__fmul_rn(__ull2float_rn(x), is1), is2);
     }
 };
 
@@ -479,14 +492,93 @@ struct FastDiv {
     }
 };
 
+// Home slot of a row in a hashed window: multiplicative hash scaled to HS
+// slots (any HS).
+template <int HS>
+__device__ __forceinline__ int table_home(int row) {
+    return (int)(((uint64_t)((uint32_t)row * 0x9E3779B1u) * (uint64_t)HS) >> 32);
+}
+
+// Add q at `row`: slot row - r0 in an identity window (rows of the window
+// span at most HS slots; every writer of a slot stores the same row), else
+// linear probing from the row's hash, an empty slot claimed by
+// compare-and-swap.  A probe run of PMAX slots sets *ovf and adds nothing.
+template <int HS, bool IDENT>
+__device__ __forceinline__ void acc_add(int row, unsigned long long q, int r0, int* keys,
+                                        unsigned long long* vals, int* ovf) {
+    if (IDENT) {
+        const unsigned h = (unsigned)(row - r0);
+        if (h >= (unsigned)HS) {  // cannot happen: a window's segments hold rows in [r0, r1)
+            *ovf = 2;
+            return;
+        }
+        keys[h] = row;
+        red_add_u64(vals + h, q);
+        return;
+    }
+    int h = table_home<HS>(row);
+    for (int p = 0; p < PMAX; ++p) {
+        int k = *reinterpret_cast<volatile int*>(keys + h);
+        if (k == KEY_EMPTY) {
+            k = cas_shared(keys + h, KEY_EMPTY, row);
+            if (k == KEY_EMPTY) k = row;
+        }
+        if (k == row) {
+            red_add_u64(vals + h, q);
+            return;
+        }
+        if (++h == HS) h = 0;
+    }
+    *ovf = 1;
+}
+
+// Expected entries per source and window below which a window walks its
+// sources one per lane instead of one per warp.
+constexpr int LANE_MODE_MAX = 12;
+
+// The ranking keys of a window's table after extraction (0: empty slot;
+// thread t takes slots t, t + T, ...).
+template <int T, int HS>
+struct KeyEnum {
+    const uint64_t* vk;
+    __device__ int count(uint64_t tau) const {
+        int c = 0;
+        for (int h = threadIdx.x; h < HS; h += T) c += vk[h] > tau;
+        return c;
+    }
+    __device__ void emit(uint64_t tau, uint64_t* dst, int base) const {
+        for (int h = threadIdx.x; h < HS; h += T) {
+            const uint64_t k = vk[h];
+            if (k > tau) dst[base++] = k;
+        }
+    }
+};
+
+struct ExpandArgs {
+    CscView A;
+    PruneParams pp;
+    ExpandBuffers b;
+    int conf;
+    int plan;
+};
+
+template <int T, int HS>
+struct ExpandLayout {
+    static constexpr size_t bytes(int ksel) {
+        return (size_t)HS * 12 + (size_t)(ksel + HS) * 8 + 256 * 4 + 256 * 8 + sizeof(WinShared);
+    }
+};
+
 template <int T, int HS, int MINB>
 __global__ void __launch_bounds__(T, MINB) k_expand(ExpandArgs a) {
     const int PLAN = a.plan;  // distinct rows a window is planned for
     constexpr int IPT = 8;
-    static_assert(HS >= (T / 32) * 128, "the row sort's counters fit in the table");
+    static_assert(HS >= (T / 32) * 256, "the row sort's counters fit in the key array");
     extern __shared__ __align__(16) unsigned char smem[];
-    uint64_t* tab = reinterpret_cast<uint64_t*>(smem);
-    uint64_t* top = tab + HS;
+    unsigned long long* vals = reinterpret_cast<unsigned long long*>(smem);
+    int* keys = reinterpret_cast<int*>(vals + HS);
+    uint64_t* vkeys = reinterpret_cast<uint64_t*>(vals);  // ranking keys after extraction
+    uint64_t* top = reinterpret_cast<uint64_t*>(keys + HS);
     const int ksel = a.pp.ksel;
     const int topcap = ksel + HS;  // a window adds at most HS candidates
     unsigned* hist = reinterpret_cast<unsigned*>(top + topcap);
@@ -505,7 +597,11 @@ __global__ void __launch_bounds__(T, MINB) k_expand(ExpandArgs a) {
     const int wbeg = ctr->bin_off[a.conf * NZ], wend = ctr->bin_off[a.conf * NZ + NZ];
     if (ctr->err & ERR_STAGING) return;  // the iteration is redone without the graph
 
-    for (int i = tid; i < HS; i += T) tab[i] = SLOT_EMPTY;
+    for (int i = tid; i < HS; i += T) {
+        keys[i] = KEY_EMPTY;
+        vals[i] = 0ull;
+    }
+    const float theta = a.pp.theta;
     for (;;) {
         if (tid == 0) sh->item = atomicAdd(&ctr->conf_ctr[a.conf], 1);
         __syncthreads();
@@ -537,9 +633,6 @@ __global__ void __launch_bounds__(T, MINB) k_expand(ExpandArgs a) {
         const int64_t flops_j = b.flops[j];
         int64_t est = b.est[j];
         if (est < 1) est = 1;
-        // column sum of B_*j from the identity sum_i (AA)_ij = sum_k a_kj sum_i a_ik
-        // (FP64; exact up to FP64 rounding, independent of the FP32 accumulation)
-        double s_sum = 0.0;
         for (int i = tid; i < d; i += T) {
             const int k = A.rowidx[cb + i];
             const int64_t ks = A.colptr[k];
@@ -548,7 +641,14 @@ __global__ void __launch_bounds__(T, MINB) k_expand(ExpandArgs a) {
             meta.len[i] = (int)(A.colptr[k + 1] - ks);
             meta.cur[i] = 0;
             meta.akj[i] = akj;
-            s_sum += (double)akj * b.colsum[k];
+        }
+        // column sum of B_*j from the identity sum_i (AA)_ij = sum_k a_kj sum_i a_ik,
+        // FP64 in a fixed order (warp 0, lane-strided, butterfly), independent of T
+        if (warp == 0) {
+            double s = 0.0;
+            for (int i = lane; i < d; i += 32) s += (double)A.val[cb + i] * b.colsum[A.rowidx[cb + i]];
+            s = warp_sum(s);
+            if (lane == 0) sh->red = s;
         }
         // ---- plan: about est / PLAN windows of equal row width.  With bucket
         // space the products go to per-window buckets, and a window that
@@ -564,19 +664,31 @@ __global__ void __launch_bounds__(T, MINB) k_expand(ExpandArgs a) {
             if (nw64 > wmax) nw64 = wmax;
             bucket = true;
         }
-        const int width = (int)(((int64_t)span + nw64 - 1) / nw64);
+        int width = (int)(((int64_t)span + nw64 - 1) / nw64);
+        if (width < HS && span > width) {
+            // a window of at most HS rows has a slot per row (no hashing): use the
+            // widest such windows
+            const int64_t nid = ((int64_t)span + HS - 1) / HS;
+            if (nid < nw64) {
+                nw64 = nid;
+                width = (int)(((int64_t)span + nw64 - 1) / nw64);
+            }
+        }
         const int nwin = (int)(((int64_t)span + width - 1) / width);
         int ntop = 0;
         uint64_t tau = 0;
-        double s_mt = 0.0;
+        unsigned long long s_mt = 0;
         long long s_t = 0, s_n = 0;
         FastDiv fdiv;
         fdiv.init((uint32_t)width);
         __syncthreads();
+        const double S = sh->red;
+        FixScale fx;
+        fx.init(S);
 
         if (bucket) {
             // ---- count the products of every window (counters in the table's key array) ----
-            int* wcnt = reinterpret_cast<int*>(tab);  // nwin <= HS counters each
+            int* wcnt = reinterpret_cast<int*>(vals);  // nwin <= HS counters each
             int* wcur = wcnt + HS;
             for (int i = tid; i < nwin; i += T) wcnt[i] = 0;
             if (tid == 0) sh->next = 0;
@@ -679,7 +791,7 @@ __global__ void __launch_bounds__(T, MINB) k_expand(ExpandArgs a) {
                 }
             }
             __syncthreads();
-            for (int i = tid; i < HS; i += T) tab[i] = SLOT_EMPTY;
+            for (int i = tid; i < HS; i += T) vals[i] = 0ull;
         }
 
         // ---- windows ----
@@ -740,6 +852,19 @@ __global__ void __launch_bounds__(T, MINB) k_expand(ExpandArgs a) {
             const int F0 = sh->pf0, F1 = sh->pf1, R0 = sh->pr0, R1 = sh->pr1;
             const bool RS = sh->prs != 0;
             int* ovfp = &sh->ovf2[par];
+            // rows of this window: a bucket window (or its split piece) or the cursor range;
+            // at most HS rows wide, it maps row - wr0 to its slot (no hashing)
+            const int wr0 = bucket ? (RS ? R0 : lo + F0 * width) : R0;
+            const int wr1 =
+                bucket ? (RS ? R1 : (int)min((int64_t)lo + (int64_t)(F0 + 1) * width, (int64_t)hiE))
+                       : R1;
+            const bool ident = wr1 - wr0 <= HS;
+            auto add = [&](int row, unsigned long long q) {
+                if (ident)
+                    acc_add<HS, true>(row, q, wr0, keys, vals, ovfp);
+                else
+                    acc_add<HS, false>(row, q, wr0, keys, vals, ovfp);
+            };
             // ---- 1. insert the products of the window ----
             if (bucket) {
                 const int bs = woff[F0], be = woff[F1];
@@ -758,7 +883,7 @@ __global__ void __launch_bounds__(T, MINB) k_expand(ExpandArgs a) {
                     for (int u = 0; u < 4; ++u) {
                         bool valid = rr[u] >= 0;
                         if (RS) valid = valid && rr[u] >= R0 && rr[u] < R1;
-                        if (valid) table_add<HS>(rr[u], pv[u], tab, ovfp);
+                        if (valid) add(rr[u], fx.qv(pv[u]));
                     }
                 }
             } else if (lane_mode) {
@@ -772,7 +897,7 @@ __global__ void __launch_bounds__(T, MINB) k_expand(ExpandArgs a) {
                     for (; pos < len; ++pos) {
                         const int row = __ldg(rows + pos);
                         if (row >= R1) break;
-                        table_add<HS>(row, __ldg(vv + pos) * akj, tab, ovfp);
+                        add(row, fx.q(__ldg(vv + pos), akj));
                     }
                     nxt[kidx] = pos;
                 }
@@ -792,7 +917,7 @@ __global__ void __launch_bounds__(T, MINB) k_expand(ExpandArgs a) {
                         const int p = pos + lane;
                         const int row = p < len ? __ldg(rows + p) : INT_MAX;
                         const bool valid = row < R1;
-                        if (valid) table_add<HS>(row, __ldg(vv + p) * akj, tab, ovfp);
+                        if (valid) add(row, fx.q(__ldg(vv + p), akj));
                         const int nin = __popc(__ballot_sync(FULL, valid));
                         pos += nin;
                         if (nin < 32) break;
@@ -802,7 +927,11 @@ __global__ void __launch_bounds__(T, MINB) k_expand(ExpandArgs a) {
             }
             __syncthreads();
             if (*ovfp) {
-                for (int i = tid; i < HS; i += T) tab[i] = SLOT_EMPTY;
+                for (int i = tid; i < HS; i += T) {
+                    keys[i] = KEY_EMPTY;
+                    vals[i] = 0ull;
+                }
+                if (*ovfp == 2 && tid == 0) set_err2(ctr, ERR_INTERNAL);  // cannot happen
                 if (tid == 0) {
                     atomicAdd(&ctr->splits, 1ull);
                     if (bucket && !rowsplit) {
@@ -819,31 +948,34 @@ __global__ void __launch_bounds__(T, MINB) k_expand(ExpandArgs a) {
                 }
                 continue;
             }
-            // ---- 2. statistics and candidates ----
-            TableEnum<T, HS> en{tab};
+            // ---- 2. statistics and candidates: every entry becomes its ranking key
+            // in place (exact statistics from the fixed-point sums), row keys cleared ----
+            KeyEnum<T, HS> en{vkeys};
             int c = 0, cnt = 0;
-            float pmt = 0.0f;  // HS / T terms per thread and window
             for (int h = tid; h < HS; h += T) {
-                const uint64_t x = tab[h];
-                if (x != SLOT_EMPTY) {
-                    const float v = slot_val(x);
+                const int row = keys[h];
+                if (row != KEY_EMPTY) {
+                    const unsigned long long q = vals[h];
+                    const float v = fx.value(q);
+                    const uint64_t key = make_key(v, row);
                     ++cnt;
-                    if (v >= a.pp.theta) {
+                    if (v >= theta) {
                         ++s_t;
-                        pmt += v;
+                        s_mt += q;
                     }
-                    c += slot_key(x) > tau;
+                    c += key > tau;
+                    vkeys[h] = key;
+                    keys[h] = KEY_EMPTY;
                 }
             }
             s_n += cnt;
-            s_mt += (double)pmt;
             {
                 const int wc = warp_sum(cnt);
                 if (lane == 0 && wc) atomicAdd(&sh->went2[par], wc);
             }
             append_candidates<T, IPT>(en, top, topcap, ksel, ntop, tau, c, hist, sh);
             // ---- 3. clear the table ----
-            for (int i = tid; i < HS; i += T) tab[i] = SLOT_EMPTY;
+            for (int i = tid; i < HS; i += T) vkeys[i] = 0ull;
             if (!bucket) {  // cursors advance past the window
                 int32_t* t = cur;
                 cur = nxt;
@@ -879,18 +1011,19 @@ __global__ void __launch_bounds__(T, MINB) k_expand(ExpandArgs a) {
                 publish(par ^ 1);
             }
         }
-        double dv[2] = {s_sum, s_mt};
-        long long qv[2] = {s_t, s_n};
-        block_sum<T>(dv, 2, qv, 2, &sh->bs);
+        double dv[1] = {0.0};
+        long long qv[3] = {s_t, s_n, (long long)s_mt};
+        block_sum<T>(dv, 0, qv, 3, &sh->bs);
+        const double MT = ldexp((double)(unsigned long long)qv[2], -fx.f);
         int mstar = 0;
         double ch = 0.0;
         const int64_t obase = b.off[j];
         // the table's key array is free here: radix counters of the row sort
-        finish_column<T, IPT, false>(top, ntop, topcap, a.pp, dv[0], dv[1], qv[0], b.cap[j],
+        finish_column<T, IPT, false>(top, ntop, topcap, a.pp, S, MT, qv[0], b.cap[j],
                                      b.tmp_row + (obase - b.tmp_off0),
                                      b.tmp_val + (obase - b.tmp_off0), hist, mhist, sh, ctr, lo,
-                                     span, reinterpret_cast<unsigned*>(tab), &mstar, &ch);
-        for (int i = tid; i < (T / 32) * 128; i += T) tab[i] = SLOT_EMPTY;
+                                     span, reinterpret_cast<unsigned*>(keys), &mstar, &ch);
+        for (int i = tid; i < (T / 32) * 256; i += T) keys[i] = KEY_EMPTY;
         if (tid == 0) {
             b.kept[j] = mstar;
             b.chaos[j] = ch;
@@ -1068,3 +1201,4 @@ void launch_prune(const CscView& B, const PruneParams& pp, const ExpandBuffers& 
 }
 
 }  // namespace mcl
+

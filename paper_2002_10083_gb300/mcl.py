@@ -24,6 +24,7 @@ STATUS = {0: "MCL_OK", 1: "MCL_ERR_INVALID", 2: "MCL_ERR_OOM", 3: "MCL_ERR_CUDA"
 OPT_SIZING, OPT_CONF_MASK, OPT_VALIDATE, OPT_EST_SCALE, OPT_ITERATION, OPT_PHASE_BUDGET = 1, 2, 3, 4, 5, 6
 OPT_COHEN_KEYS, OPT_COHEN_SEED = 7, 8
 OPT_GRAPH, OPT_GRAPH_CAP = 9, 10
+OPT_SMALL_MAX, OPT_TABLE, OPT_PLAN, OPT_GROUP_BUDGET = 11, 12, 13, 14
 SIZING_COHEN = 3
 SIZING_PARAMS, SIZING_EXACT, SIZING_FLOPS = -1, 0, 1
 MAX_SELECT_K = 4096
@@ -57,7 +58,8 @@ class _Stats(ctypes.Structure):
                 ("ms_compact", ctypes.c_float), ("ms_chaos", ctypes.c_float),
                 ("ms_total", ctypes.c_float), ("bins_used", ctypes.c_int32),
                 ("iterations", ctypes.c_int32), ("phases", ctypes.c_int32),
-                ("graph_replays", ctypes.c_int32), ("exact_from", ctypes.c_int32)]
+                ("graph_replays", ctypes.c_int32), ("exact_from", ctypes.c_int32),
+                ("groups", ctypes.c_int32)]
 
 
 _ALLOC = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
