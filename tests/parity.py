@@ -4,10 +4,12 @@ The oracle is fed the same input the GPU saw (its FP32 values widened to
 FP64).  Per column:
 
 * kept patterns must be identical, except entries that are ambiguous
-  because FP32 accumulation may legitimately flip them: within ``rtol`` of
-  the prune threshold, of the K-th largest value, or whose cumulative mass
-  (in oracle order, before or including the entry) is within ``rtol`` of
-  the recovery target p * s;
+  because FP32 rounding may legitimately flip them: within ``rtol`` of the
+  prune threshold, of the K-th largest value, of the value at the cut (the
+  last kept or first dropped value in oracle order, whichever rule set the
+  cut: two entries equal in FP32 are ranked by row), or whose cumulative
+  mass (in oracle order, before or including the entry) is within ``rtol``
+  of the recovery target p * s;
 * values must agree to ``rtol`` relative.  Where an ambiguous entry made
   the kept sets differ, the expected values are the oracle's B values
   inflated and renormalised over the GPU's kept set.
@@ -69,6 +71,8 @@ def compare_iteration(A_in, G_out, prm: oracle.Params, cols=None, rtol=1e-5, inf
             s = float(res.bsum[c])
             target = prm.p * s
             bK = tvals[K - 1] if nt >= K else None
+            # the values on both sides of the oracle's cut
+            b_cut = [tvals[x] for x in (m - 1, m) if 0 <= x < nt]
             cum_incl = np.cumsum(tvals)
             cum_before = cum_incl - tvals
             diff = set(g_rows.tolist()) ^ set(o_rows.tolist())
@@ -82,6 +86,8 @@ def compare_iteration(A_in, G_out, prm: oracle.Params, cols=None, rtol=1e-5, inf
                 amb = abs(b - prm.theta) <= rtol * prm.theta
                 if bK is not None:
                     amb = amb or abs(b - bK) <= rtol * bK
+                for bc in b_cut:
+                    amb = amb or abs(b - bc) <= rtol * bc
                 if target > 0:
                     amb = amb or abs(cum_before[i] - target) <= rtol * target
                     amb = amb or abs(cum_incl[i] - target) <= rtol * target

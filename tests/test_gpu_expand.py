@@ -554,6 +554,60 @@ def test_zipf4m_degree_law_column_batched_sampled():
     assert rep.ok(), rep.failures[:5]
 
 
+def _host_ram_gb():
+    try:
+        for line in open("/proc/meminfo"):
+            if line.startswith("MemTotal:"):
+                return int(line.split()[1]) / 2 ** 20
+    except OSError:
+        pass
+    return 0.0
+
+
+@pytest.mark.slow
+def test_zipf4m_iterations_1_and_2_full_size_sampled():
+    """The 4M-vertex workload at its stated size, as configured (learned
+    sizing, column batches under a 180 GB staging budget): iterations 1 and
+    2 against the oracle fed the GPU's own input on 20,000 random columns
+    each (plus the 40 with the most products), and every output column sums
+    to 1."""
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    if _host_ram_gb() < 160:
+        pytest.skip("needs about 160 GB of host memory for the oracle's copy of A_1")
+    from paper_2002_10083_gb300 import estimator, mcl
+    A = synth.config("zipf4m").with_val32()
+    ctx = mcl.Context(0)
+    try:
+        estimator.install(ctx)
+        ctx.set_option(mcl.OPT_PHASE_BUDGET, 180 << 30)
+        prm = _prm(theta=1e-4, K=1100, p=0.9)
+        prm.use_estimator = 1
+        D = _dev(A)
+        Hin = A
+        for it in (1, 2):
+            ctx.set_option(mcl.OPT_ITERATION, it)
+            out, ch = ctx.expand(D, prm)
+            torch.cuda.synchronize()
+            G = out.to_host()
+            sums = np.add.reduceat(G.val, G.colptr[:-1]) if G.nnz else np.zeros(0)
+            nzc = np.diff(G.colptr) > 0
+            np.testing.assert_allclose(sums[nzc], 1.0, rtol=0, atol=2e-5)
+            deg = np.diff(Hin.colptr)
+            fl = np.zeros(Hin.n, np.int64)
+            np.add.at(fl, np.repeat(np.arange(Hin.n), deg), deg[Hin.rowidx])
+            rng = np.random.default_rng(4000 + it)
+            cols = np.unique(np.concatenate([rng.choice(Hin.n, 20000, replace=False),
+                                             np.argsort(-fl)[:40]])).astype(np.int32)
+            rep, _ = compare_iteration(Hin, G, _oprm(prm), cols=cols, rtol=RTOL)
+            assert rep.ok(), (it, rep.failures[:5])
+            assert ctx.stats()["flops"] == int(fl.sum())
+            del D
+            D, Hin = out, G
+    finally:
+        ctx.close()
+
+
 def test_checkpointed_run_equals_mcl_run(ctx, tmp_path):
     """A run stopped after 3 iterations and resumed from its checkpoint ends
     with mcl_run's iterations and clusters."""
