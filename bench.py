@@ -220,6 +220,79 @@ def _time_form(ctx, D, prm, steps, stream, torch, mcl):
     return e0.elapsed_time(e1) / steps, statistics.median(ms_num), st
 
 
+def time_e2e(ctx, A, prm, nnz_out, dev, steps, torch, mcl):
+    """End-to-end steps through the C ABI with pinned host buffers (see run_gpu)."""
+    n = A.n
+    cuda = f"cuda:{dev}"
+    hcp = torch.from_numpy(np.ascontiguousarray(A.colptr, np.int64)).pin_memory()
+    hri = torch.from_numpy(np.ascontiguousarray(A.rowidx, np.int32)).pin_memory()
+    hva = torch.from_numpy(np.ascontiguousarray(A.val, np.float32)).pin_memory()
+    dcp = torch.empty_like(hcp, device=cuda)
+    dri = torch.empty_like(hri, device=cuda)
+    dva = torch.empty_like(hva, device=cuda)
+    Dh = mcl.DeviceCSC(n, dcp, dri, dva)
+    # two pinned result buffers, used alternately (the result size is fixed for a fixed input)
+    cap = nnz_out + 1
+    bufs = [(torch.empty(n + 1, dtype=torch.int64, pin_memory=True),
+             torch.empty(cap, dtype=torch.int32, pin_memory=True),
+             torch.empty(cap, dtype=torch.float32, pin_memory=True)) for _ in range(2)]
+    stream = torch.cuda.current_stream(dev)
+    copy_stream = torch.cuda.Stream(dev)
+    in_bytes = hcp.numel() * 8 + hri.numel() * 4 + hva.numel() * 4
+    out_bytes = 0
+    # achieved link bandwidth, one upload and one download timed alone
+    e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+    torch.cuda.synchronize()
+    e0.record(stream)
+    dcp.copy_(hcp, non_blocking=True)
+    dri.copy_(hri, non_blocking=True)
+    dva.copy_(hva, non_blocking=True)
+    e1.record(stream)
+    out, _ = ctx.expand(Dh, prm)
+    m = int(out.rowidx.numel())
+    e2.record(stream)
+    cp, ri, va = bufs[0]
+    cp.copy_(out.colptr, non_blocking=True)
+    ri[:m].copy_(out.rowidx, non_blocking=True)
+    va[:m].copy_(out.val, non_blocking=True)
+    e3 = torch.cuda.Event(enable_timing=True)
+    e3.record(stream)
+    torch.cuda.synchronize()
+    h2d_gbs = in_bytes / (e0.elapsed_time(e1) * 1e-3) / 1e9
+    d2h_gbs = ((n + 1) * 8 + 8 * m) / (e2.elapsed_time(e3) * 1e-3) / 1e9
+    del out
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i in range(steps):
+        dcp.copy_(hcp, non_blocking=True)
+        dri.copy_(hri, non_blocking=True)
+        dva.copy_(hva, non_blocking=True)
+        out, _ = ctx.expand(Dh, prm)
+        m = int(out.rowidx.numel())
+        if m > cap:  # never for a fixed input; kept correct regardless
+            copy_stream.synchronize()
+            cap = m
+            bufs = [(b[0], torch.empty(cap, dtype=torch.int32, pin_memory=True),
+                     torch.empty(cap, dtype=torch.float32, pin_memory=True)) for b in bufs]
+        ev = torch.cuda.Event()
+        ev.record(stream)
+        cp, ri, va = bufs[i % 2]
+        with torch.cuda.stream(copy_stream):
+            copy_stream.wait_event(ev)
+            cp.copy_(out.colptr, non_blocking=True)
+            ri[:m].copy_(out.rowidx, non_blocking=True)
+            va[:m].copy_(out.val, non_blocking=True)
+        for t in (out.colptr, out.rowidx, out.val):
+            t.record_stream(copy_stream)
+        out_bytes = (n + 1) * 8 + m * 4 + m * 4
+        del out
+    copy_stream.synchronize()
+    torch.cuda.synchronize()
+    ms = (time.perf_counter() - t0) * 1000.0 / steps
+    return {"ms": ms, "steps": steps, "h2d_bytes": in_bytes, "d2h_bytes": out_bytes,
+            "h2d_gbs": h2d_gbs, "d2h_gbs": d2h_gbs}
+
+
 def run_gpu(args):
     import torch
     rank, local, world = _env_rank()
@@ -283,44 +356,18 @@ def run_gpu(args):
     ms_c, t_num_c, st_c = _time_form(ctx, D, prm_plain, args.steps, stream, torch, mcl)
     ctx.set_option(mcl.OPT_SIZING, mcl.SIZING_PARAMS)
 
-    # end to end through the C ABI with host buffers (pinned): H2D of A,
-    # the iteration, D2H of the resulting matrix
-    hcp = torch.from_numpy(A.colptr).pin_memory()
-    hri = torch.from_numpy(A.rowidx).pin_memory()
-    hva = torch.from_numpy(A.val.astype(np.float32)).pin_memory()
-    e2e_steps = 0 if args.no_e2e else max(1, min(args.steps, 3))
-    out_bytes = 0
-    # pinned host buffers for the result, allocated once outside the timed
-    # region (the result's size is the same every step: the timed steps above)
-    cap_out = int(nnz_out) + 1
-    ocp = torch.empty(n + 1, dtype=torch.int64, pin_memory=True)
-    ori = torch.empty(cap_out, dtype=torch.int32, pin_memory=True) if e2e_steps else None
-    ova = torch.empty(cap_out, dtype=torch.float32, pin_memory=True) if e2e_steps else None
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        Dh = mcl.DeviceCSC(n, hcp.to(f"cuda:{dev}", non_blocking=True),
-                           hri.to(f"cuda:{dev}", non_blocking=True),
-                           hva.to(f"cuda:{dev}", non_blocking=True))
-        out, ch = ctx.expand(Dh, prm_main)
-        m = int(out.rowidx.numel())
-        if m > cap_out:  # never for a fixed input; kept correct regardless
-            ori = torch.empty(m, dtype=torch.int32, pin_memory=True)
-            ova = torch.empty(m, dtype=torch.float32, pin_memory=True)
-            cap_out = m
-        ocp.copy_(out.colptr, non_blocking=True)
-        ori[:m].copy_(out.rowidx, non_blocking=True)
-        ova[:m].copy_(out.val, non_blocking=True)
-        torch.cuda.synchronize()
-        out_bytes = (n + 1) * 8 + m * 4 + m * 4
-        del out, Dh
-    e2e_ms = (time.perf_counter() - t0) * 1000.0 / max(e2e_steps, 1)
-    in_bytes = hcp.numel() * 8 + hri.numel() * 4 + hva.numel() * 4
+    # end to end through the C ABI with host buffers (pinned): every step
+    # copies A host -> device, runs the iteration and copies the resulting
+    # matrix device -> host.  The device input buffers and the pinned result
+    # buffers are allocated before the timed region; the result's copy runs on
+    # a second stream, overlapping the next step's upload and iteration.
+    e2e = None if args.no_e2e else time_e2e(ctx, A, prm_main, int(nnz_out), dev,
+                                              max(1, min(args.steps, 5)), torch, mcl)
 
     if rank != 0:
         return 0
     gflops = job_gflops(flops, ms, world)
-    e2e_gflops = job_gflops(flops, e2e_ms, world) if e2e_steps else None
+    in_bytes = A.colptr.nbytes + A.rowidx.nbytes + A.val.astype(np.float32).nbytes
     peak, peak_kind = _peaks()
     b_alg = 8 * nnz + 8 * flops + 8 * nnz_out + 16 * n
     achieved = b_alg / (t_num / 1000.0) / 1e9
@@ -363,9 +410,14 @@ def run_gpu(args):
                      "algorithmic_bytes": b_alg, "kernel_ms": round(t_num, 3),
                      "peak_kind": peak_kind},
         "cpu_baseline": cpu,
-        "e2e": ({"value": round(e2e_gflops, 2), "unit": "GFLOP/s", "h2d_bytes_per_step": in_bytes,
-                 "d2h_bytes_per_step": out_bytes, "ms_per_step": round(e2e_ms, 3)}
-                if e2e_steps else None),
+        "e2e": ({"value": round(job_gflops(flops, e2e["ms"], world), 2), "unit": "GFLOP/s",
+                 "h2d_bytes_per_step": e2e["h2d_bytes"], "d2h_bytes_per_step": e2e["d2h_bytes"],
+                 "ms_per_step": round(e2e["ms"], 3), "steps": e2e["steps"],
+                 "h2d_gbs": round(e2e["h2d_gbs"], 1), "d2h_gbs": round(e2e["d2h_gbs"], 1),
+                 "vs_device_step": round(e2e["ms"] / ms, 3),
+                 "how": "pinned host buffers; H2D of A and the iteration on the launch stream, "
+                        "D2H of the result on a second stream overlapping the next step"}
+                if e2e else None),
         "gpu_launches": int(launches),
         "clocks": clocks,
         "stage_ms": {k: round(v, 3) for k, v in st.items() if k.startswith("ms_")},
@@ -377,92 +429,250 @@ def run_gpu(args):
     return 0
 
 
+def _clocked(fn):
+    """Run fn() with nvidia-smi clock sampling; returns (fn's result, clocks)."""
+    clk = ClockSampler(os.environ.get("CUDA_VISIBLE_DEVICES", "0").split(",")[0])
+    clk.start()
+    time.sleep(0.3)
+    try:
+        res = fn()
+    finally:
+        clocks = clk.stop()
+    return res, clocks
+
+
 def run_batched(args):
     """Batched MCL to convergence over independent components (each stops on
     its own chaos), or column-batched iterations of the 4M-vertex graph."""
+    if args.workload == "zipf4m":
+        return run_zipf4m(args)
     import torch
-    from paper_2002_10083_gb300 import estimator, mcl, synth
+    from paper_2002_10083_gb300 import autotune, estimator, mcl, synth
     t0 = time.time()
-    if args.workload == "batch4096":
-        A = synth.config("batch4096", seed=0, ncomp=args.ncomp)
-        offs = A.comp_offsets
-        prm = mcl.Params(threshold=1e-4, select_k=1100, recover_pct=0.9, inflation=2.0,
-                         chaos_eps=1e-3, max_iters=args.max_iters, batched=1,
-                         use_estimator=0)
-    else:
-        A = synth.config("zipf4m", seed=0, **({"n": args.n} if args.n else {}))
-        offs = None
-        prm = mcl.Params(threshold=1e-4, select_k=1100, recover_pct=0.9, inflation=2.0,
-                         chaos_eps=1e-3, max_iters=args.max_iters, use_estimator=1)
+    A = synth.config("batch4096", seed=0, ncomp=args.ncomp)
+    offs = A.comp_offsets
     gen_s = time.time() - t0
-    D = mcl.DeviceCSC.from_host(synth.CSC(n=A.n, colptr=A.colptr, rowidx=A.rowidx,
-                                          val=A.val.astype(np.float32)))
+    A32 = synth.CSC(n=A.n, colptr=A.colptr, rowidx=A.rowidx, val=A.val.astype(np.float32))
+    D = mcl.DeviceCSC.from_host(A32)
     ctx = mcl.Context(0)
     # the estimator trained on this workload's graph family (other seeds), if there is one
-    est_path = args.estimator or (estimator.BATCH_WEIGHTS if args.workload == "batch4096" and
-                                  os.path.exists(estimator.BATCH_WEIGHTS)
+    est_path = args.estimator or (estimator.BATCH_WEIGHTS if os.path.exists(estimator.BATCH_WEIGHTS)
                                   else estimator.DEFAULT_WEIGHTS)
     est_meta = estimator.install(ctx, est_path)
-    from paper_2002_10083_gb300 import autotune
     tuned = autotune.apply(ctx, autotune.load(), torch.cuda.get_device_name(0),
                            autotune.class_of_host(A))
-    if args.phase_budget_gb:
-        ctx.set_option(mcl.OPT_PHASE_BUDGET, int(args.phase_budget_gb * (1 << 30)))
+    if args.group_budget_gb:
+        ctx.set_option(mcl.OPT_GROUP_BUDGET, int(args.group_budget_gb * (1 << 30)))
     torch.cuda.synchronize()
+    peak, peak_kind = _peaks()
 
-    def timed_run(graph: int, offsets, use_est: int):
+    def timed_run(graph: int, batched: int, use_est: int):
         ctx.set_option(mcl.OPT_GRAPH, graph)
-        p = mcl.Params(threshold=prm.threshold, select_k=prm.select_k,
-                       recover_pct=prm.recover_pct, inflation=prm.inflation,
-                       chaos_eps=prm.chaos_eps, max_iters=prm.max_iters,
-                       batched=1 if offsets is not None else 0, use_estimator=use_est)
+        p = mcl.Params(threshold=1e-4, select_k=1100, recover_pct=0.9, inflation=2.0,
+                       chaos_eps=1e-3, max_iters=args.max_iters, batched=batched,
+                       use_estimator=use_est)
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record()
-        out = ctx.run(D, p, comp_offsets=offsets, keep_final=False)
+        out = ctx.run(D, p, comp_offsets=offs, keep_final=False)
         e1.record()
         torch.cuda.synchronize()
         return out, e0.elapsed_time(e1), ctx.stats()
 
     def summary(res, ms, st):
         lab_, iters_, hist_, _, nc_ = res
-        return {"ms_total": round(ms, 1), "iterations": iters_,
-                "iters_per_s": round(iters_ / (ms / 1000.0), 4), "converged": not nc_,
-                "graph_replays": int(st["graph_replays"])}
+        sec = ms / 1000.0
+        return {"seconds": round(sec, 2), "iterations": iters_,
+                "iters_per_s": round(iters_ / sec, 4), "converged": not nc_,
+                "gflops": round(2.0 * st["flops_run"] / sec / 1e9, 2),
+                "multiply_adds": int(st["flops_run"]),
+                "hbm_frac_alg": round(st["alg_bytes_run"] / sec / 1e9 / peak, 4),
+                "graph_replays": int(st["graph_replays"]), "groups": int(st["groups"])}
 
-    forms = {}
-    if offs is not None:
-        # plain: the whole block-diagonal matrix until its global chaos < eps,
-        # exact sizing, eager loop; batched: per-component retirement with
-        # iterations after the first replayed as CUDA graphs (exact sizing),
-        # then eager, then with the learned sizing
-        runs = [("plain", 0, None, 0), ("batched", 1, offs, 0), ("batched_eager", 0, offs, 0),
-                ("learned_batched", 1, offs, 1)]
-    else:
-        runs = [("learned", 1, None, prm.use_estimator)]
-    results = {}
-    for name, graph, o, ue in runs:
-        res, ms, st = timed_run(graph, o, ue)
-        results[name] = (res, ms, st)
+    # learned + batched (per-component retirement, iterations after the first as
+    # CUDA graph replays), the same with exact sizing, and plain: exact sizing,
+    # eager, no per-component retirement (each group of components iterates until
+    # the group's chaos < eps)
+    runs = [("learned_batched", 1, 1, 1), ("batched_exact", 1, 1, 0), ("plain", 0, 0, 0)]
+    results, forms = {}, {}
+    clocks = None
+    for name, graph, batched, ue in runs:
+        if name == "learned_batched":
+            (res, ms, st), clocks = _clocked(lambda: timed_run(graph, batched, ue))
+        else:
+            res, ms, st = timed_run(graph, batched, ue)
+        results[name] = res
         forms[name] = summary(res, ms, st)
-    main_name = "learned_batched" if offs is not None else "learned"
-    (lab, iters, hist, final, notconv), ms, st = results[main_name]
-    labels_equal = {k: bool(torch.equal(v[0][0], lab)) for k, v in results.items()}
-    line = {"metric": METRIC, "workload": args.workload, "n": A.n, "nnz": A.nnz,
-            "components": None if offs is None else len(offs) - 1,
-            "form": main_name, "iterations": iters, "converged": not notconv,
-            "ms_total": round(ms, 1), "iters_per_s": round(iters / (ms / 1000.0), 4),
-            "chaos_history": [round(h, 6) for h in hist],
-            "clusters": int(len(np.unique(lab.cpu().numpy()))),
-            "last_iteration": {k: st[k] for k in ("flops", "nnz_b", "nnz_out", "phases",
-                                                  "estimator_misses")},
-            "forms": forms, "labels_equal_to_main": labels_equal,
-            "generation_s": round(gen_s, 1), "phase_budget_gb": args.phase_budget_gb,
+    lab = results["learned_batched"][0].cpu().numpy()
+    labels_equal = bool(np.array_equal(lab, results["batched_exact"][0].cpu().numpy()))
+    parity = None if args.no_check else check_batch(ctx, A32, offs, lab, results, args)
+    cpu = None if args.no_cpu_baseline else batch_cpu_baseline(A32, offs, args.cpu_seconds)
+    main = forms["learned_batched"]
+    line = {"metric": METRIC, "workload": f"batch{len(offs) - 1}: {len(offs) - 1} planted-partition "
+            "components, sizes log-uniform in [50, 50000], p_in 0.05, p_out 0.0005, weights U(0.1, 1], "
+            "K 1100, theta 1e-4, p 0.9, r 2, to per-component chaos < 1e-3",
+            "n": A.n, "nnz": A.nnz, "components": len(offs) - 1,
+            "value": main["iters_per_s"], "unit": "MCL iters/s", "higher_is_better": True,
+            "form": "learned_batched", "forms": forms,
+            "speedup_learned_batched_vs_plain": round(forms["plain"]["seconds"] / main["seconds"], 4),
+            "speedup_learned_vs_exact_batched": round(forms["batched_exact"]["seconds"] / main["seconds"], 4),
+            "labels_learned_equal_exact": labels_equal,
+            "roofline": {"bound": "hbm", "achieved": round(main["hbm_frac_alg"] * peak, 1),
+                         "peak": peak, "unit": "GB/s", "frac": main["hbm_frac_alg"],
+                         "kernel": "whole run (algorithmic bytes of every iteration / run time)",
+                         "peak_kind": peak_kind},
+            "parity": parity, "cpu_baseline": cpu, "clocks": clocks,
+            "generation_s": round(gen_s, 1), "group_budget_gb": args.group_budget_gb,
             "tuning": tuned if tuned is not None else "library defaults",
             "estimator": {"weights": os.path.basename(est_path),
                           "trained_on": est_meta.get("workload"),
                           "train_seeds": est_meta.get("train_seeds")}}
     print(json.dumps(line), flush=True)
+    ctx.close()
+    return 0
+
+
+def check_batch(ctx, A, offs, lab, results, args):
+    """Oracle parity of the batched run: clusters and iteration counts of
+    sampled small components against per-component oracle runs, and the
+    largest component's first iterations on sampled columns against the
+    oracle fed the GPU's own input (its clusters: the batched labels equal a
+    run of that component alone)."""
+    import torch
+    import oracle
+    from paper_2002_10083_gb300 import mcl
+    from tests.parity import compare_iteration
+    t0 = time.time()
+    oprm = oracle.Params(theta=float(np.float32(1e-4)), K=1100, p=float(np.float32(0.9)), r=2.0,
+                         eps=1e-3, max_iters=args.max_iters)
+    sizes = np.diff(offs)
+    rng = np.random.default_rng(7)
+    small = np.nonzero(sizes <= 300)[0]
+    pick = rng.choice(small, min(64, len(small)), replace=False)
+    big = int(np.argmax(sizes))
+    mism = []
+    for c in pick:
+        lo, hi = int(offs[c]), int(offs[c + 1])
+        sub = oracle.submatrix(A, lo, hi)
+        _, it_o, _, lab_o = oracle.run_mcl(sub, oprm)
+        if not np.array_equal(lab[lo:hi] - lo, lab_o):
+            mism.append(int(c))
+    # the largest component alone, iteration by iteration
+    lo, hi = int(offs[big]), int(offs[big + 1])
+    sub = oracle.submatrix(A, lo, hi)
+    Dc = mcl.DeviceCSC.from_host(sub)
+    prm = mcl.Params(threshold=1e-4, select_k=1100, recover_pct=0.9, inflation=2.0)
+    big_ok, big_cols = True, 0
+    for it in range(3):
+        Hin = Dc.to_host()
+        out, _ = ctx.expand(Dc, prm)
+        cols = rng.choice(hi - lo, min(200, hi - lo), replace=False).astype(np.int32)
+        rep, _ = compare_iteration(Hin, out.to_host(), oprm, cols=cols, rtol=1e-5)
+        big_ok = big_ok and rep.ok()
+        big_cols += len(cols)
+        Dc = out
+    p1 = mcl.Params(threshold=1e-4, select_k=1100, recover_pct=0.9, inflation=2.0, chaos_eps=1e-3,
+                    max_iters=args.max_iters)
+    lab1, *_ = ctx.run(mcl.DeviceCSC.from_host(sub), p1, keep_final=False)
+    big_same = bool(np.array_equal(lab1.cpu().numpy(), lab[lo:hi] - lo))
+    torch.cuda.synchronize()
+    return {"sampled_components": len(pick), "sampled_max_size": int(sizes[pick].max()),
+            "clusters_equal_oracle": len(pick) - len(mism), "mismatched_components": mism,
+            "largest_component": {"size": int(hi - lo), "iterations_checked": 3,
+                                  "columns_checked": big_cols, "values_within_1e-5": big_ok,
+                                  "batched_labels_equal_alone": big_same},
+            "seconds": round(time.time() - t0, 1)}
+
+
+def batch_cpu_baseline(A, offs, seconds):
+    """The oracle's whole loop on randomly drawn components (bounded time):
+    multiply-adds per second over the components it finished."""
+    import oracle
+    oprm = oracle.Params(theta=float(np.float32(1e-4)), K=1100, p=float(np.float32(0.9)), r=2.0,
+                         eps=1e-3, max_iters=30)
+    rng = np.random.default_rng(11)
+    sizes = np.diff(offs)
+    order = rng.permutation(np.nonzero(sizes <= 2000)[0])
+    flops, comps, vert = 0, 0, 0
+    t0 = time.perf_counter()
+    for c in order:
+        if time.perf_counter() - t0 > seconds:
+            break
+        sub = oracle.submatrix(A, int(offs[c]), int(offs[c + 1]))
+        M = sub
+        for _ in range(oprm.max_iters):
+            M, ch, res = oracle.expand(M, oprm)
+            flops += int(res.flops.sum())
+            if ch < oprm.eps:
+                break
+        comps += 1
+        vert += sub.n
+    dt = time.perf_counter() - t0
+    return {"value": round(2.0 * flops / dt / 1e9, 4), "unit": "GFLOP/s", "cores": oracle.num_threads(),
+            "kind": "oracle", "sample": f"{comps} whole components of <= 2000 vertices "
+            f"({vert} vertices) run to convergence, {dt:.1f} s"}
+
+
+def run_zipf4m(args):
+    """The 4M-vertex power-law graph: MCL iterations through mcl_expand with
+    learned sizing and column batches under the staging budget (180 GB), each
+    timed with CUDA events."""
+    import torch
+    from paper_2002_10083_gb300 import autotune, estimator, mcl
+    t0 = time.time()
+    A = make_workload("zipf4m", n=args.n)
+    gen_s = time.time() - t0
+    D = mcl.DeviceCSC.from_host(A)
+    ctx = mcl.Context(0)
+    est_meta = estimator.install(ctx, args.estimator or estimator.DEFAULT_WEIGHTS)
+    tuned = autotune.apply(ctx, autotune.load(), torch.cuda.get_device_name(0),
+                           autotune.class_of_host(A))
+    budget = args.phase_budget_gb or 180.0
+    ctx.set_option(mcl.OPT_PHASE_BUDGET, int(budget * (1 << 30)))
+    peak, peak_kind = _peaks()
+    prm = mcl.Params(threshold=1e-4, select_k=1100, recover_pct=0.9, inflation=2.0, use_estimator=1)
+    iters = []
+
+    def loop():
+        Dc = D
+        for it in range(1, args.max_iters + 1):
+            ctx.set_option(mcl.OPT_ITERATION, it)
+            nin = Dc.nnz
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            out, ch = ctx.expand(Dc, prm)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            st = ctx.stats()
+            b_alg = 8 * nin + 8 * st["flops"] + 8 * st["nnz_out"] + 16 * A.n
+            iters.append({"iteration": it, "ms": round(ms, 1), "multiply_adds": int(st["flops"]),
+                          "nnz_in": int(nin), "nnz_out": int(st["nnz_out"]),
+                          "gflops": round(2.0 * st["flops"] / (ms / 1000.0) / 1e9, 2),
+                          "numeric_ms": round(st["ms_numeric"], 1), "phases": int(st["phases"]),
+                          "hbm_frac_alg_numeric": round(b_alg / (st["ms_numeric"] / 1000.0) / 1e9 / peak, 4),
+                          "estimator_misses": int(st["estimator_misses"]), "chaos": round(ch, 6)})
+            if Dc is not D:
+                del Dc
+            Dc = out
+        return Dc
+
+    _, clocks = _clocked(loop)
+    tot_ms = sum(x["ms"] for x in iters)
+    tot_f = sum(x["multiply_adds"] for x in iters)
+    line = {"metric": METRIC, "workload": "zipf4m: 4M-vertex Zipf(2) power-law graph, mean degree ~120 "
+            "capped at 5,000, lognormal(0,1) weights; learned sizing, column batches under a "
+            f"{budget:.0f} GB staging budget, K 1100, theta 1e-4, p 0.9, r 2",
+            "n": A.n, "nnz": A.nnz, "iterations": len(iters),
+            "value": round(len(iters) / (tot_ms / 1000.0), 4), "unit": "MCL iters/s",
+            "gflops": round(2.0 * tot_f / (tot_ms / 1000.0) / 1e9, 2),
+            "seconds": round(tot_ms / 1000.0, 2), "per_iteration": iters, "clocks": clocks,
+            "generation_s": round(gen_s, 1), "phase_budget_gb": budget,
+            "tuning": tuned if tuned is not None else "library defaults",
+            "estimator": {"trained_on": est_meta.get("workload"), "train_seeds": est_meta.get("train_seeds")}}
+    print(json.dumps(line), flush=True)
+    ctx.close()
     return 0
 
 
@@ -527,7 +737,10 @@ def main():
     ap.add_argument("--max-iters", type=int, default=30)
     ap.add_argument("--estimator", default=None, help="estimator weights (.npz) for the batched runs")
     ap.add_argument("--phase-budget-gb", type=float, default=0.0,
-                    help="column-batch staging budget for zipf4m (0: one batch)")
+                    help="column-batch staging budget for zipf4m (0: 180 GB)")
+    ap.add_argument("--group-budget-gb", type=float, default=150.0,
+                    help="device bytes per group of components for batch4096 (0: one group)")
+    ap.add_argument("--no-check", action="store_true", help="skip the batch4096 oracle checks")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -111,8 +111,11 @@ typedef struct {
     int32_t exact_from;       /* mcl_run with use_estimator: first iteration sized exactly because
                                  the learned estimates of an earlier one fell short on more than
                                  1/20 of its columns (0: none) */
-    int32_t groups;           /* groups of components of the last batched mcl_run
+    int32_t groups;           /* groups of components of the last mcl_run with comp_offsets
                                  (MCL_OPT_GROUP_BUDGET; 1 when it ran as one group) */
+    int64_t flops_run;        /* last mcl_run: multiply-adds over all its iterations */
+    int64_t alg_bytes_run;    /* last mcl_run: algorithmic bytes of its iterations, each
+                                 8 nnz(A_t) + 8 flops + 8 nnz(A_t+1) + 16 n */
 } mcl_stats;
 
 /* Create a context on `device` (made current by every call).  alloc/free
@@ -245,12 +248,14 @@ mcl_status mcl_symbolic(mcl_ctx* ctx, const mcl_csc* A, int64_t* flops, int64_t*
  *  13 MCL_OPT_PLAN       entries planned per hashed window (0 = half the
  *                        table, at most 3072)
  *  14 MCL_OPT_GROUP_BUDGET  bytes of device memory one group of components
- *                        may use in a batched mcl_run; 0 (default) = one
- *                        group.  A batch whose components need more (about
- *                        32 bytes per entry of size * min(size, K_rec) plus
- *                        160 bytes per vertex) runs in consecutive groups of
- *                        whole components, each to its own convergence, with
- *                        the same results as one run.
+ *                        may use in an mcl_run with comp_offsets; 0 (default)
+ *                        = one group.  Components needing more in total
+ *                        (about 32 bytes per entry of size * min(size, K_rec)
+ *                        plus 160 bytes per vertex) run in consecutive groups
+ *                        of whole components, one group after the other.  A
+ *                        batched run gives the same results as one run; a
+ *                        run with prm->batched == 0 iterates each group until
+ *                        that group's chaos drops below chaos_eps.
  * Returns MCL_ERR_INVALID for an unknown option or value.
  */
 #define MCL_OPT_SIZING 1

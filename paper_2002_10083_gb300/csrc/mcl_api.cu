@@ -35,7 +35,8 @@ struct mcl_ctx {
     size_t bucket_budget = (size_t)32 << 30;  // bytes of product buckets (large config)
     size_t phase_budget = 0;                  // bytes of output staging per column batch (0: one)
     Buf phase_colptr;
-    DevCounters* hctr = nullptr;  // pinned host mirror
+    DevCounters* hctr = nullptr;      // mapped pinned host mirror of the device counters
+    DevCounters* hctr_dev = nullptr;  // its device address (written by a kernel, no copy engine)
     mcl_stats stats{};
     cudaEvent_t ev[8] = {};
     // options
@@ -211,7 +212,9 @@ mcl_status ensure_columns(mcl_ctx* c, int64_t n, cudaStream_t s) {
 }
 
 mcl_status read_counters(mcl_ctx* c, cudaStream_t s) {
-    CUDA_TRY(c, cudaMemcpyAsync(c->hctr, c->ctr.p, sizeof(DevCounters), cudaMemcpyDeviceToHost, s));
+    // a kernel writes the mirror, so that the read does not queue on a copy
+    // engine behind the caller's large transfers on other streams
+    launch_copy_counters((const DevCounters*)c->ctr.p, c->hctr_dev, s);
     CUDA_TRY(c, cudaStreamSynchronize(s));
     return MCL_OK;
 }
@@ -272,7 +275,8 @@ mcl_status mcl_create(mcl_ctx** out, int device, mcl_alloc_fn alloc, mcl_free_fn
     c->user = alloc_user;
     if (cudaSetDevice(device) != cudaSuccess ||
         cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
-        cudaMallocHost((void**)&c->hctr, sizeof(DevCounters)) != cudaSuccess) {
+        cudaHostAlloc((void**)&c->hctr, sizeof(DevCounters), cudaHostAllocMapped) != cudaSuccess ||
+        cudaHostGetDevicePointer((void**)&c->hctr_dev, c->hctr, 0) != cudaSuccess) {
         cudaGetLastError();
         delete c;
         return MCL_ERR_CUDA;
@@ -454,7 +458,7 @@ static mcl_status expand_impl(mcl_ctx* c, const mcl_csc* A, const mcl_params* pr
                 int64_t capb = (int64_t)(c->bucket_budget / ((size_t)g * 8));
                 if (capb > maxf) capb = maxf;
                 if (capb >= 1024 && ensure(c, c->bucket_row, (size_t)g * capb * 8, s) &&
-                    ensure(c, c->woff, (size_t)g * (WINDOW_MAX + 1) * 4, s)) {
+                    ensure(c, c->woff, (size_t)g * 2 * (WINDOW_MAX + 1) * 4, s)) {
                     bq.bucket_row = (int32_t*)c->bucket_row.p;
                     bq.woff = (int32_t*)c->woff.p;
                     bq.bucket_cap = capb;
@@ -977,7 +981,7 @@ static void static_iteration(mcl_ctx* c, const mcl_params* prm, const PruneParam
         launch_logcf(n, b.flops, b.bnnz, (float*)c->prev_logcf.p, s);
         launch_iter_bump((int32_t*)c->iter_dev.p, s);
     }
-    cudaMemcpyAsync(c->hctr, c->ctr.p, sizeof(DevCounters), cudaMemcpyDeviceToHost, s);
+    launch_copy_counters((const DevCounters*)c->ctr.p, c->hctr_dev, s);
 }
 
 // Allocates the replay buffers, moves `cur` (the output of the first
@@ -1019,7 +1023,7 @@ static mcl_status graph_prepare(mcl_ctx* c, const mcl_params* prm, const PrunePa
             return fail(c, MCL_ERR_OOM, "estimator scratch allocation failed");
     }
     if (capb >= 1024 && ensure(c, c->bucket_row, (size_t)g1 * capb * 8, s) &&
-        ensure(c, c->woff, (size_t)g1 * (WINDOW_MAX + 1) * 4, s)) {
+        ensure(c, c->woff, (size_t)g1 * 2 * (WINDOW_MAX + 1) * 4, s)) {
         // exact per-CTA capacity recorded in the buffer sizes
         c->bucket_row.bytes = (size_t)g1 * capb * 8;
     } else {
@@ -1181,14 +1185,20 @@ mcl_status mcl_run(mcl_ctx* c, const mcl_csc* A0, const int32_t* comp_offsets, i
     if (comp_offsets && ncomp < 1) return fail(c, MCL_ERR_INVALID, "ncomp must be >= 1");
     cudaStream_t s = (cudaStream_t)stream;
     const bool batched = comp_offsets && prm->batched;
-    if (batched) {
+    if (comp_offsets) {
         if (comp_offsets[0] != 0 || comp_offsets[ncomp] != A0->n)
             return fail(c, MCL_ERR_INVALID, "comp_offsets must run from 0 to n");
         for (int q = 0; q < ncomp; ++q)
             if (comp_offsets[q + 1] < comp_offsets[q])
                 return fail(c, MCL_ERR_INVALID, "comp_offsets must be nondecreasing");
-        CUDA_TRY(c, cudaSetDevice(c->device));
+    }
+    if (!c->in_group) {
         c->stats.groups = 1;
+        c->stats.flops_run = 0;
+        c->stats.alg_bytes_run = 0;
+    }
+    if (comp_offsets) {
+        CUDA_TRY(c, cudaSetDevice(c->device));
         if (c->group_budget > 0 && !c->in_group) {
             // consecutive groups of whole components within the budget
             PruneParams gp;
@@ -1209,6 +1219,8 @@ mcl_status mcl_run(mcl_ctx* c, const mcl_csc* A0, const int32_t* comp_offsets, i
                 return run_groups(c, A0, comp_offsets, gcut, prm, labels, iters, chaos_hist,
                                   final_out, s);
         }
+    }
+    if (batched) {
         const size_t n1 = (size_t)A0->n + 1;
         if (!ensure(c, c->comp_off, (size_t)(ncomp + 1) * 4, s) ||
             !ensure(c, c->comp_of_col, n1 * 4, s) || !ensure(c, c->comp_bits, (size_t)ncomp * 8, s) ||
@@ -1276,6 +1288,7 @@ mcl_status mcl_run(mcl_ctx* c, const mcl_csc* A0, const int32_t* comp_offsets, i
                 cudaStreamWaitEvent(G.gs, e, 0);
                 cudaEventDestroy(e);
             }
+            const int64_t in_nnz = cur.nnz;
             CUDA_TRY(c, cudaGraphLaunch(G.x[graph_at], G.gs));
             count_launches((int)G.kernels);
             CUDA_TRY(c, cudaStreamSynchronize(G.gs));
@@ -1340,6 +1353,8 @@ mcl_status mcl_run(mcl_ctx* c, const mcl_csc* A0, const int32_t* comp_offsets, i
             }
             mcl_stats& S = c->stats;
             S.flops = (int64_t)c->hctr->flops;
+            S.flops_run += S.flops;
+            S.alg_bytes_run += 8 * (in_nnz + S.flops + cur.nnz) + 16 * (int64_t)cur.n;
             S.nnz_in = G.cap;
             S.nnz_b = (int64_t)c->hctr->nnz_b;
             S.nnz_out = cur.nnz;
@@ -1364,6 +1379,11 @@ mcl_status mcl_run(mcl_ctx* c, const mcl_csc* A0, const int32_t* comp_offsets, i
         }
         st = expand_impl(c, &cur, prm, &nxt, &ch, s, act);
         const int64_t it_misses = st ? 0 : c->stats.estimator_misses;
+        if (!st) {
+            mcl_stats& S = c->stats;
+            S.flops_run += S.flops;
+            S.alg_bytes_run += 8 * (S.nnz_in + S.flops + S.nnz_out) + 16 * (int64_t)cur.n;
+        }
         if (!st && batched) {
             // per-component chaos of this iteration; converged components retire
             cudaMemsetAsync(c->comp_bits.p, 0, (size_t)ncomp * 8, s);

@@ -148,6 +148,7 @@ void launch_comp_chaos(int32_t n, const int32_t* comp_of_col, const uint8_t* act
 void launch_comp_retire(int32_t ncomp, const unsigned long long* comp_bits, double eps,
                         uint8_t* comp_active, DevCounters* ctr, cudaStream_t s);
 void launch_staging_guard(DevCounters* ctr, int64_t capacity, cudaStream_t s);
+void launch_copy_counters(const DevCounters* src, DevCounters* dst, cudaStream_t s);
 void launch_block_colptr(const int64_t* colptr, int32_t lo, int32_t ng, int64_t* colptr_g,
                          cudaStream_t s);
 void launch_add_i32(const int32_t* src, int64_t m, int32_t delta, int32_t* dst, cudaStream_t s);

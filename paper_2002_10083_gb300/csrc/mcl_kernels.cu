@@ -891,6 +891,20 @@ void launch_place_colptr(const int64_t* colptr_g, int32_t lo, int32_t ng, int64_
     count_launches(1);
 }
 
+// The device counters into host-mapped memory, one 8-byte word per thread.
+__global__ void k_copy_counters(const DevCounters* src, DevCounters* dst) {
+    constexpr int W = (int)(sizeof(DevCounters) / 8);
+    static_assert(sizeof(DevCounters) % 8 == 0, "counters are whole 8-byte words");
+    const int i = threadIdx.x;
+    if (i < W) reinterpret_cast<unsigned long long*>(dst)[i] =
+        reinterpret_cast<const unsigned long long*>(src)[i];
+}
+
+void launch_copy_counters(const DevCounters* src, DevCounters* dst, cudaStream_t s) {
+    k_copy_counters<<<1, (int)((sizeof(DevCounters) / 8 + 31) / 32 * 32), 0, s>>>(src, dst);
+    count_launches(1);
+}
+
 __global__ void k_fill_colptr(int32_t n, int64_t* colptr) {
     int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (j <= n) colptr[j] = 0;

@@ -593,7 +593,9 @@ __global__ void __launch_bounds__(T, MINB) k_expand(ExpandArgs a) {
     // per-CTA bucket of (row, bits(product)) pairs
     int2* bkt = b.bucket_row ? reinterpret_cast<int2*>(b.bucket_row) + (int64_t)blockIdx.x * b.bucket_cap
                              : nullptr;
-    int32_t* woff = b.woff ? b.woff + (int64_t)blockIdx.x * (WINDOW_MAX + 1) : nullptr;
+    // window starts and ends in the bucket (per CTA: WINDOW_MAX + 1 of each)
+    int32_t* woff = b.woff ? b.woff + (int64_t)blockIdx.x * 2 * (WINDOW_MAX + 1) : nullptr;
+    int32_t* wlim = woff ? woff + (WINDOW_MAX + 1) : nullptr;
     const int wbeg = ctr->bin_off[a.conf * NZ], wend = ctr->bin_off[a.conf * NZ + NZ];
     if (ctr->err & ERR_STAGING) return;  // the iteration is redone without the graph
 
@@ -687,110 +689,140 @@ __global__ void __launch_bounds__(T, MINB) k_expand(ExpandArgs a) {
         fx.init(S);
 
         if (bucket) {
-            // ---- count the products of every window (counters in the table's key array) ----
             int* wcnt = reinterpret_cast<int*>(vals);  // nwin <= HS counters each
             int* wcur = wcnt + HS;
-            for (int i = tid; i < nwin; i += T) wcnt[i] = 0;
-            if (tid == 0) sh->next = 0;
-            __syncthreads();
-            for (;;) {
-                int kidx = 0;
-                if (lane == 0) kidx = atomicAdd(&sh->next, 1);
-                kidx = __shfl_sync(FULL, kidx, 0);
-                if (kidx >= d) break;
-                const int len = meta.len[kidx];
-                const int32_t* rows = A.rowidx + meta.ks[kidx];
-                for (int pb = 0; pb < len; pb += 128) {
-                    int rr[4];
+            // Scatter (row, a_ik * a_kj) into the window buckets from the cursors wcur;
+            // with a capacity capw per window (window w owns [w capw, (w + 1) capw))
+            // a run that would pass its window's end sets sh->next2[1] and writes
+            // nothing past it.
+            auto scatter = [&](int capw) {
+                if (tid == 0) sh->next = 0;
+                __syncthreads();
+                for (;;) {
+                    int kidx = 0;
+                    if (lane == 0) kidx = atomicAdd(&sh->next, 1);
+                    kidx = __shfl_sync(FULL, kidx, 0);
+                    if (kidx >= d) break;
+                    const int len = meta.len[kidx];
+                    const int64_t ks = meta.ks[kidx];
+                    const int32_t* rows = A.rowidx + ks;
+                    const float* vv = A.val + ks;
+                    const float akj = meta.akj[kidx];
+                    for (int pb = 0; pb < len; pb += 128) {
+                        int rr[4];
+                        float pv[4];
 #pragma unroll
-                    for (int c = 0; c < 4; ++c) {
-                        const int p = pb + 32 * c + lane;
-                        rr[c] = p < len ? __ldg(rows + p) : 0;
-                    }
+                        for (int c = 0; c < 4; ++c) {
+                            const int p = pb + 32 * c + lane;
+                            rr[c] = p < len ? __ldg(rows + p) : 0;
+                            pv[c] = p < len ? __ldg(vv + p) : 0.0f;
+                        }
 #pragma unroll
-                    for (int c = 0; c < 4; ++c) {
-                        // rows are sorted, so equal windows form runs of lanes
-                        const bool v = pb + 32 * c + lane < len;
-                        const unsigned act = __ballot_sync(FULL, v);  // a prefix of the lanes
-                        if (act == 0u) break;
-                        const uint32_t w = v ? fdiv.div((uint32_t)(rr[c] - lo)) : 0xFFFFFFFFu;
-                        const uint32_t wp = __shfl_up_sync(FULL, w, 1);
-                        const bool head = v && (lane == 0 || wp != w);
-                        const unsigned heads = __ballot_sync(FULL, head);
-                        if (head) {
-                            const unsigned after = heads & ~((2u << lane) - 1u);
-                            const int end = after ? __ffs(after) - 1 : __popc(act);
-                            atomicAdd(wcnt + w, end - lane);
+                        for (int c = 0; c < 4; ++c) {
+                            const bool v = pb + 32 * c + lane < len;
+                            const unsigned act = __ballot_sync(FULL, v);  // a prefix of the lanes
+                            if (act == 0u) break;
+                            const int row = rr[c];
+                            const uint32_t w = v ? fdiv.div((uint32_t)(row - lo)) : 0xFFFFFFFFu;
+                            const uint32_t wp = __shfl_up_sync(FULL, w, 1);
+                            const bool head = v && (lane == 0 || wp != w);
+                            const unsigned heads = __ballot_sync(FULL, head);
+                            int base = 0;
+                            if (head) {
+                                const unsigned after = heads & ~((2u << lane) - 1u);
+                                const int end = after ? __ffs(after) - 1 : __popc(act);
+                                base = atomicAdd(wcur + w, end - lane);
+                                if (capw > 0 && base + (end - lane) > ((int)w + 1) * capw)
+                                    sh->next2[1] = 1;
+                            }
+                            // the head of this lane's run: the highest head at or below it
+                            const int hl = 31 - __clz(heads & ((2u << lane) - 1u));
+                            base = __shfl_sync(FULL, base, hl);
+                            if (v) {
+                                const int pos = base + lane - hl;
+                                if (capw == 0 || pos < ((int)w + 1) * capw)
+                                    bkt[pos] = make_int2(row, __float_as_int(pv[c] * akj));
+                            }
                         }
                     }
                 }
-            }
-            __syncthreads();
-            // ---- window offsets (exclusive scan), scatter cursors ----
-            {
-                const int per = (nwin + T - 1) / T;
-                const int i0 = min(nwin, tid * per), i1 = min(nwin, i0 + per);
-                int c = 0;
-                for (int i = i0; i < i1; ++i) c += wcnt[i];
-                int tot;
-                int run = block_scan_excl<T>(c, &tot, sh->wsm);
-                for (int i = i0; i < i1; ++i) {
-                    woff[i] = run;
-                    wcur[i] = run;
-                    run += wcnt[i];
-                }
-                if (tid == 0) woff[nwin] = tot;
-                if (tid == 0 && (int64_t)tot != flops_j) set_err2(ctr, ERR_INTERNAL);
-            }
-            if (tid == 0) sh->next = 0;
-            __syncthreads();
-            // ---- scatter (row, a_ik * a_kj) into the window buckets ----
-            for (;;) {
-                int kidx = 0;
-                if (lane == 0) kidx = atomicAdd(&sh->next, 1);
-                kidx = __shfl_sync(FULL, kidx, 0);
-                if (kidx >= d) break;
-                const int len = meta.len[kidx];
-                const int64_t ks = meta.ks[kidx];
-                const int32_t* rows = A.rowidx + ks;
-                const float* vv = A.val + ks;
-                const float akj = meta.akj[kidx];
-                for (int pb = 0; pb < len; pb += 128) {
-                    int rr[4];
-                    float pv[4];
-#pragma unroll
-                    for (int c = 0; c < 4; ++c) {
-                        const int p = pb + 32 * c + lane;
-                        rr[c] = p < len ? __ldg(rows + p) : 0;
-                        pv[c] = p < len ? __ldg(vv + p) : 0.0f;
+                __syncthreads();
+            };
+            // products per window of equal row width are near their mean for
+            // rows spread over the span: try fixed capacities first
+            const int64_t capw64 = ((flops_j + nwin - 1) / nwin) * 5 / 4 + 64;
+            bool counted = true;
+            if (capw64 * nwin <= b.bucket_cap) {
+                const int capw = (int)capw64;
+                for (int i = tid; i < nwin; i += T) wcur[i] = i * capw;
+                if (tid == 0) sh->next2[1] = 0;
+                __syncthreads();
+                scatter(capw);
+                counted = sh->next2[1] != 0;  // a window was fuller than its capacity
+                if (!counted)
+                    for (int i = tid; i < nwin; i += T) {
+                        woff[i] = i * capw;
+                        wlim[i] = wcur[i];
                     }
+                __syncthreads();
+            }
+            if (counted) {
+                // ---- count the products of every window ----
+                for (int i = tid; i < nwin; i += T) wcnt[i] = 0;
+                if (tid == 0) sh->next = 0;
+                __syncthreads();
+                for (;;) {
+                    int kidx = 0;
+                    if (lane == 0) kidx = atomicAdd(&sh->next, 1);
+                    kidx = __shfl_sync(FULL, kidx, 0);
+                    if (kidx >= d) break;
+                    const int len = meta.len[kidx];
+                    const int32_t* rows = A.rowidx + meta.ks[kidx];
+                    for (int pb = 0; pb < len; pb += 128) {
+                        int rr[4];
 #pragma unroll
-                    for (int c = 0; c < 4; ++c) {
-                        const bool v = pb + 32 * c + lane < len;
-                        const unsigned act = __ballot_sync(FULL, v);  // a prefix of the lanes
-                        if (act == 0u) break;
-                        const int row = rr[c];
-                        const uint32_t w = v ? fdiv.div((uint32_t)(row - lo)) : 0xFFFFFFFFu;
-                        const uint32_t wp = __shfl_up_sync(FULL, w, 1);
-                        const bool head = v && (lane == 0 || wp != w);
-                        const unsigned heads = __ballot_sync(FULL, head);
-                        int base = 0;
-                        if (head) {
-                            const unsigned after = heads & ~((2u << lane) - 1u);
-                            const int end = after ? __ffs(after) - 1 : __popc(act);
-                            base = atomicAdd(wcur + w, end - lane);
+                        for (int c = 0; c < 4; ++c) {
+                            const int p = pb + 32 * c + lane;
+                            rr[c] = p < len ? __ldg(rows + p) : 0;
                         }
-                        // the head of this lane's run: the highest head at or below it
-                        const int hl = 31 - __clz(heads & ((2u << lane) - 1u));
-                        base = __shfl_sync(FULL, base, hl);
-                        if (v) {
-                            const int pos = base + lane - hl;
-                            bkt[pos] = make_int2(row, __float_as_int(pv[c] * akj));
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) {
+                            // rows are sorted, so equal windows form runs of lanes
+                            const bool v = pb + 32 * c + lane < len;
+                            const unsigned act = __ballot_sync(FULL, v);  // a prefix of the lanes
+                            if (act == 0u) break;
+                            const uint32_t w = v ? fdiv.div((uint32_t)(rr[c] - lo)) : 0xFFFFFFFFu;
+                            const uint32_t wp = __shfl_up_sync(FULL, w, 1);
+                            const bool head = v && (lane == 0 || wp != w);
+                            const unsigned heads = __ballot_sync(FULL, head);
+                            if (head) {
+                                const unsigned after = heads & ~((2u << lane) - 1u);
+                                const int end = after ? __ffs(after) - 1 : __popc(act);
+                                atomicAdd(wcnt + w, end - lane);
+                            }
                         }
                     }
                 }
+                __syncthreads();
+                // ---- window offsets (exclusive scan), scatter cursors ----
+                {
+                    const int per = (nwin + T - 1) / T;
+                    const int i0 = min(nwin, tid * per), i1 = min(nwin, i0 + per);
+                    int c = 0;
+                    for (int i = i0; i < i1; ++i) c += wcnt[i];
+                    int tot;
+                    int run = block_scan_excl<T>(c, &tot, sh->wsm);
+                    for (int i = i0; i < i1; ++i) {
+                        woff[i] = run;
+                        wcur[i] = run;
+                        run += wcnt[i];
+                        wlim[i] = run;
+                    }
+                    if (tid == 0 && (int64_t)tot != flops_j) set_err2(ctr, ERR_INTERNAL);
+                }
+                __syncthreads();
+                scatter(0);
             }
-            __syncthreads();
             for (int i = tid; i < HS; i += T) vals[i] = 0ull;
         }
 
@@ -808,7 +840,7 @@ __global__ void __launch_bounds__(T, MINB) k_expand(ExpandArgs a) {
         const bool lane_mode =
             !bucket && (double)flops_j * (double)width < (double)LANE_MODE_MAX * (double)d * (double)span;
         auto plan = [&](int f) {  // thread 0 only
-            while (f < nwin && woff[f + 1] == woff[f]) ++f;  // empty windows
+            while (f < nwin && wlim[f] == woff[f]) ++f;  // empty windows
             f0 = f;
             f1 = f;
             rowsplit = false;
@@ -867,7 +899,7 @@ __global__ void __launch_bounds__(T, MINB) k_expand(ExpandArgs a) {
             };
             // ---- 1. insert the products of the window ----
             if (bucket) {
-                const int bs = woff[F0], be = woff[F1];
+                const int bs = woff[F0], be = wlim[F0];
                 // four products per lane in flight before the table updates
                 for (int pb = bs + warp * 128; pb < be; pb += T * 4) {
                     int rr[4];

@@ -59,7 +59,8 @@ class _Stats(ctypes.Structure):
                 ("ms_total", ctypes.c_float), ("bins_used", ctypes.c_int32),
                 ("iterations", ctypes.c_int32), ("phases", ctypes.c_int32),
                 ("graph_replays", ctypes.c_int32), ("exact_from", ctypes.c_int32),
-                ("groups", ctypes.c_int32)]
+                ("groups", ctypes.c_int32), ("flops_run", ctypes.c_int64),
+                ("alg_bytes_run", ctypes.c_int64)]
 
 
 _ALLOC = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
