@@ -314,6 +314,8 @@ def run_gpu(args):
     from paper_2002_10083_gb300 import autotune
     tuned = autotune.apply(ctx, autotune.load(), torch.cuda.get_device_name(dev),
                            autotune.class_of_host(A))
+    if args.bucket_budget_gb:
+        ctx.set_option(mcl.OPT_BUCKET_BUDGET, int(args.bucket_budget_gb * (1 << 30)))
     prm_plain = mcl.Params(**PARAMS)
     prm_learn = mcl.Params(**PARAMS, use_estimator=1)
     prm_main = prm_plain if args.form == "plain" else prm_learn
@@ -741,6 +743,8 @@ def main():
     ap.add_argument("--group-budget-gb", type=float, default=150.0,
                     help="device bytes per group of components for batch4096 (0: one group)")
     ap.add_argument("--no-check", action="store_true", help="skip the batch4096 oracle checks")
+    ap.add_argument("--bucket-budget-gb", type=float, default=0.0,
+                    help="device memory of the numeric pass's product buckets (0: library default)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -256,6 +256,10 @@ mcl_status mcl_symbolic(mcl_ctx* ctx, const mcl_csc* A, int64_t* flops, int64_t*
  *                        batched run gives the same results as one run; a
  *                        run with prm->batched == 0 iterates each group until
  *                        that group's chaos drops below chaos_eps.
+ *  15 MCL_OPT_BUCKET_BUDGET  bytes of device memory for the numeric pass's
+ *                        per-window product buckets (default 32 GiB); columns
+ *                        whose products do not fit a CTA's share walk their
+ *                        sources with cursors instead (same results)
  * Returns MCL_ERR_INVALID for an unknown option or value.
  */
 #define MCL_OPT_SIZING 1
@@ -272,6 +276,7 @@ mcl_status mcl_symbolic(mcl_ctx* ctx, const mcl_csc* A, int64_t* flops, int64_t*
 #define MCL_OPT_TABLE 12
 #define MCL_OPT_PLAN 13
 #define MCL_OPT_GROUP_BUDGET 14
+#define MCL_OPT_BUCKET_BUDGET 15
 mcl_status mcl_set_option(mcl_ctx* ctx, int option, int64_t value);
 
 /*

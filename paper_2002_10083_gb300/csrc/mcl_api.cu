@@ -354,6 +354,10 @@ mcl_status mcl_set_option(mcl_ctx* c, int option, int64_t value) {
             if (value < 0 || value > 3072) return fail(c, MCL_ERR_INVALID, "plan in [0, 3072]");
             c->plan = (int)value;
             return MCL_OK;
+        case 15:  // bytes of product buckets of the numeric pass
+            if (value < 0) return fail(c, MCL_ERR_INVALID, "bad bucket budget");
+            c->bucket_budget = (size_t)value;
+            return MCL_OK;
         case 14:  // device bytes one group of components may use in a batched mcl_run
             if (value < 0) return fail(c, MCL_ERR_INVALID, "bad group budget");
             c->group_budget = (size_t)value;

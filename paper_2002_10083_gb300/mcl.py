@@ -24,7 +24,7 @@ STATUS = {0: "MCL_OK", 1: "MCL_ERR_INVALID", 2: "MCL_ERR_OOM", 3: "MCL_ERR_CUDA"
 OPT_SIZING, OPT_CONF_MASK, OPT_VALIDATE, OPT_EST_SCALE, OPT_ITERATION, OPT_PHASE_BUDGET = 1, 2, 3, 4, 5, 6
 OPT_COHEN_KEYS, OPT_COHEN_SEED = 7, 8
 OPT_GRAPH, OPT_GRAPH_CAP = 9, 10
-OPT_SMALL_MAX, OPT_TABLE, OPT_PLAN, OPT_GROUP_BUDGET = 11, 12, 13, 14
+OPT_SMALL_MAX, OPT_TABLE, OPT_PLAN, OPT_GROUP_BUDGET, OPT_BUCKET_BUDGET = 11, 12, 13, 14, 15
 SIZING_COHEN = 3
 SIZING_PARAMS, SIZING_EXACT, SIZING_FLOPS = -1, 0, 1
 MAX_SELECT_K = 4096
