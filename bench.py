@@ -394,9 +394,10 @@ def run_gpu(args):
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "n": n, "nnz": nnz, "flops_per_step": flops,
                    "nnz_b": nnz_b, "nnz_out": nnz_out,
-                   "form": main_name + (" (MLP sizing; estimator trained on seeds %s, held-out "
-                                        "median |log ratio| %.4f)" % (
-                                            "1-20", meta.get("eval", {}).get("median_abs_log_ratio", -1))
+                   "form": main_name + (" (MLP sizing; one estimator trained on power-law graphs of "
+                                        "100k-1M vertices and planted-partition batches, the bench "
+                                        "graph held out; held-out median |log ratio| %.4f)" % (
+                                            meta.get("eval_stats", {}).get("median_abs_log_ratio", -1))
                                         if main_name == "learned" else " (exact symbolic sizing)"),
                    "l2": "inputs larger than L2 (A is %.0f MB)" % (in_bytes / 1e6),
                    "tuning": tuned if tuned is not None else "library defaults",
@@ -458,8 +459,7 @@ def run_batched(args):
     D = mcl.DeviceCSC.from_host(A32)
     ctx = mcl.Context(0)
     # the estimator trained on this workload's graph family (other seeds), if there is one
-    est_path = args.estimator or (estimator.BATCH_WEIGHTS if os.path.exists(estimator.BATCH_WEIGHTS)
-                                  else estimator.DEFAULT_WEIGHTS)
+    est_path = args.estimator or estimator.DEFAULT_WEIGHTS
     est_meta = estimator.install(ctx, est_path)
     tuned = autotune.apply(ctx, autotune.load(), torch.cuda.get_device_name(0),
                            autotune.class_of_host(A))

@@ -25,9 +25,13 @@ import torch
 from . import mcl, synth
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-DEFAULT_WEIGHTS = os.path.join(HERE, "estimator_zipf.npz")
-# weights trained on the batched planted-partition family (256-component batches)
-BATCH_WEIGHTS = os.path.join(HERE, "estimator_batch.npz")
+# one network for every workload: trained on power-law graphs of 100k to 1M
+# vertices (two degree laws) and on batches of planted-partition components
+DEFAULT_WEIGHTS = os.path.join(HERE, "estimator_mix.npz")
+# the default mixed training and held-out sets: workload, keyword arguments, seeds
+TRAIN_MIX = "zipf1m:n=100000:1-3,zipf1m:n=200000:1-3,zipf1m:n=400000:1-3,zipf1m:1-6," \
+            "zipf4m:n=1000000:1-2,batch4096:ncomp=256:1-6"
+EVAL_MIX = "zipf1m:n=400000:100-101,zipf1m:100-101,batch4096:ncomp=256:100-101"
 NH = 64
 SHAPES = [("W1", (NH, mcl.NFEATURES)), ("b1", (NH,)), ("W2", (NH, NH)), ("b2", (NH,)),
           ("W3", (2, NH)), ("b3", (2,))]
@@ -165,55 +169,76 @@ def _gen(args):
     return synth.CSC(n=A.n, colptr=A.colptr, rowidx=A.rowidx, val=A.val.astype(np.float32))
 
 
+def parse_mix(spec: str):
+    """'workload[:key=value...]:a-b,...' -> [(workload, kwargs, seed), ...]."""
+    out = []
+    for item in spec.split(","):
+        parts = item.strip().split(":")
+        name, rest = parts[0], parts[1:]
+        a, b = rest[-1].split("-")
+        kw = {}
+        for kv in rest[:-1]:
+            k, v = kv.split("=")
+            kw[k] = int(v)
+        out.extend((name, kw, s) for s in range(int(a), int(b) + 1))
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser(description="train the learned nnz estimator")
-    ap.add_argument("--train-seeds", default="1-20")
-    ap.add_argument("--eval-seeds", default="100-104")
-    ap.add_argument("--workload", default="zipf1m")
+    ap.add_argument("--train", default=TRAIN_MIX, help="training graphs (see parse_mix)")
+    ap.add_argument("--eval", default=EVAL_MIX, help="held-out graphs")
     ap.add_argument("--iterations", type=int, default=3)
     ap.add_argument("--sample", type=int, default=200_000)
-    ap.add_argument("--epochs", type=int, default=8)
+    ap.add_argument("--epochs", type=int, default=10)
     ap.add_argument("--quantile", type=float, default=0.98)
     ap.add_argument("--procs", type=int, default=8)
-    ap.add_argument("--ncomp", type=int, default=None, help="components of a batch4096 graph")
     ap.add_argument("--out", default=DEFAULT_WEIGHTS)
     args = ap.parse_args()
-
-    def seeds(s):
-        a, b = s.split("-")
-        return list(range(int(a), int(b) + 1))
-
-    tr, ev = seeds(args.train_seeds), seeds(args.eval_seeds)
+    tr, ev = parse_mix(args.train), parse_mix(args.eval)
     t0 = time.time()
     # graphs are generated in worker processes started before any CUDA call
     import multiprocessing as mp
     with mp.get_context("spawn").Pool(args.procs) as pool:
-        kw = {"ncomp": args.ncomp} if args.ncomp else {}
-        graphs = pool.map(_gen, [(args.workload, s, kw) for s in tr + ev])
+        graphs = pool.map(_gen, [(name, seed, kw) for name, kw, seed in tr + ev])
     print(f"generated {len(graphs)} graphs in {time.time() - t0:.0f}s", flush=True)
     ctx = mcl.Context(0)
-    Xs, Ts = [], []
-    for i, A in enumerate(graphs[:len(tr)]):
-        X, T = collect(ctx, A, args.iterations, args.sample, seed=i)
-        Xs.append(X)
-        Ts.append(T)
-    X, T = torch.cat(Xs), torch.cat(Ts)
-    Xe, Te = [], []
-    for i, A in enumerate(graphs[len(tr):]):
-        X2, T2 = collect(ctx, A, args.iterations, args.sample, seed=1000 + i)
-        Xe.append(X2)
-        Te.append(T2)
-    Xe, Te = torch.cat(Xe), torch.cat(Te)
+
+    def gather(items, gs, seed0):
+        Xs, Ts, per = [], [], []
+        for i, ((name, kw, seed), A) in enumerate(zip(items, gs)):
+            X, T = collect(ctx, A, args.iterations, args.sample, seed=seed0 + i)
+            Xs.append(X)
+            Ts.append(T)
+            per.append((name, kw, seed, X.shape[0]))
+        return torch.cat(Xs), torch.cat(Ts), per
+
+    X, T, _ = gather(tr, graphs[:len(tr)], 0)
+    Xe, Te, per_e = gather(ev, graphs[len(tr):], 1000)
     print(f"collected {X.shape[0]} train / {Xe.shape[0]} eval samples in {time.time() - t0:.0f}s",
           flush=True)
     wb, norm, hist = train(ctx, X, T, epochs=args.epochs, log=lambda s: print(s, flush=True))
     tr_stats, _ = evaluate(ctx, X, T, wb, norm)
     ev_stats, ratio = evaluate(ctx, Xe, Te, wb, norm)
+    # held-out quality per graph family and size
+    groups = {}
+    at = 0
+    for name, kw, seed, m in per_e:
+        key = name + "".join(f":{k}={v}" for k, v in sorted(kw.items()))
+        groups.setdefault(key, []).append((at, at + m))
+        at += m
+    per_group = {}
+    for key, spans in groups.items():
+        idx = torch.cat([torch.arange(a, b, device=Xe.device) for a, b in spans])
+        st, _ = evaluate(ctx, Xe[idx].contiguous(), Te[idx].contiguous(), wb, norm)
+        per_group[key] = st
     safety = max(1.0, float(torch.quantile(ratio.float(), args.quantile).item()))
-    meta = {"workload": args.workload, "ncomp": args.ncomp, "train_seeds": tr, "eval_seeds": ev,
-            "iterations": args.iterations, "samples_per_iteration": args.sample,
-            "epochs": args.epochs, "train": tr_stats, "eval": ev_stats, "loss_history": hist,
-            "safety_quantile": args.quantile, "safety": safety}
+    meta = {"workload": "mix", "train": [f"{n}:{kw}:{s}" for n, kw, s in tr],
+            "eval": [f"{n}:{kw}:{s}" for n, kw, s in ev], "iterations": args.iterations,
+            "samples_per_iteration": args.sample, "epochs": args.epochs, "train_stats": tr_stats,
+            "eval_stats": ev_stats, "eval_by_family": per_group, "loss_history": hist,
+            "safety_quantile": args.quantile, "safety": safety,
+            "train_seeds": sorted({s for _, _, s in tr})}
     save(args.out, wb, norm, safety, meta)
     print(json.dumps(meta), flush=True)
 
