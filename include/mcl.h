@@ -347,6 +347,36 @@ mcl_status mcl_estimate(mcl_ctx* ctx, const mcl_csc* A, int64_t* est, void* stre
 mcl_status mcl_cohen_estimate(mcl_ctx* ctx, const mcl_csc* A, int32_t keys, uint64_t seed,
                               float* est, void* stream);
 
+/*
+ * One MCL iteration with the inner dimension of the expansion split into
+ * `nstages` blocks and the partial products combined by the binary merge
+ * (Section IV, "Binary merge"; Algorithm 2).  Stage t forms, unpruned and
+ * sorted by row, P_t = A(:, K_t) A(K_t, :) for the block K_t of rows
+ * [(t-1) n / nstages, t n / nstages) of the right operand; P_t is pushed on
+ * a stack, and when t is even the top nmerges + 1 lists are popped and
+ * merged (summed) into one (nmerges = the number of times t halves evenly),
+ * as in Algorithm 2; lists left on the stack at the end are merged last.
+ * The merged B = A A is pruned, inflated and renormalised as mcl_expand does.
+ * Partial products carry the exact fixed-point sums of mcl_expand (the same
+ * per-column scale), so `out` equals mcl_expand's result bit for bit; the
+ * point of the call is the merge schedule and its memory (stats).
+ * nstages in [1, 4096].  out allocated as in mcl_expand; chaos: optional
+ * host pointer.  stats: optional host pointer.  Synchronises `stream` after
+ * every stage and merge (to size their outputs).
+ */
+typedef struct {
+    int32_t stages;
+    int32_t merges;                  /* merges of the binary schedule (the final one included) */
+    int64_t partial_entries;         /* sum over stages of nnz(P_t): what a multiway merge holds */
+    int64_t binary_peak_entries;     /* entries of the largest merge of the binary schedule */
+    int64_t live_peak_entries;       /* most entries the binary schedule holds at once (stack,
+                                        inputs and output of a merge) */
+    int64_t merged_entries;          /* nnz(A A) */
+} mcl_merge_stats;
+#define MCL_SPLIT_MAX_STAGES 4096
+mcl_status mcl_expand_split(mcl_ctx* ctx, const mcl_csc* A, const mcl_params* prm, int32_t nstages,
+                            mcl_csc* out, double* chaos, mcl_merge_stats* stats, void* stream);
+
 /* Statistics of the last mcl_expand / mcl_run on ctx. */
 mcl_status mcl_get_stats(mcl_ctx* ctx, mcl_stats* stats);
 

@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libmcl.so")
 SOURCES = ["mcl_api.cu", "mcl_kernels.cu", "mcl_numeric.cu", "mcl_cc.cu", "mcl_estimator.cu",
-           "mcl_noalloc.cu", "mcl_cohen.cu"]
+           "mcl_noalloc.cu", "mcl_cohen.cu", "mcl_split.cu"]
 HEADERS = ["mcl_device.cuh", "mcl_internal.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -62,6 +62,8 @@ struct mcl_ctx {
     int cohen_r = 8;
     uint64_t cohen_seed = 2002;
     Buf cohen_m, cohen_e;
+    // inner-dimension split
+    Buf split_bsum, split_cnt, split_scratch;
 };
 
 namespace {
@@ -297,6 +299,7 @@ void mcl_destroy(mcl_ctx* c) {
                   &c->bucket, &c->work,   &c->kept,    &c->chaos,   &c->bnnz, &c->tmp_row,
                   &c->tmp_val, &c->cursors, &c->scan,  &c->ctr,     &c->active, &c->mlp_w,
                   &c->mlp_norm, &c->colmax, &c->feats, &c->prev_logcf, &c->cohen_m, &c->cohen_e,
+                  &c->split_bsum, &c->split_cnt, &c->split_scratch,
                   &c->iter_dev};
     for (Buf* b : all) dev_free(c, b->p, 0);
     cudaDeviceSynchronize();
@@ -642,6 +645,214 @@ mcl_status mcl_expand(mcl_ctx* c, const mcl_csc* A, const mcl_params* prm, mcl_c
                       double* chaos, void* stream) {
     if (!c) return MCL_ERR_INVALID;
     return expand_impl(c, A, prm, out, chaos, (cudaStream_t)stream, nullptr);
+}
+
+// A partial (or merged) product: row-sorted columns of exact fixed-point sums.
+struct Part {
+    int64_t* colptr = nullptr;
+    int32_t* rowidx = nullptr;
+    unsigned long long* val = nullptr;
+    int64_t nnz = 0;
+};
+
+static void free_part(mcl_ctx* c, Part& p, cudaStream_t s) {
+    dev_free(c, p.colptr, s);
+    dev_free(c, p.rowidx, s);
+    dev_free(c, p.val, s);
+    p = Part{};
+}
+
+mcl_status mcl_expand_split(mcl_ctx* c, const mcl_csc* A, const mcl_params* prm, int32_t nstages,
+                            mcl_csc* out, double* chaos, mcl_merge_stats* stats, void* stream) {
+    if (!c) return MCL_ERR_INVALID;
+    PruneParams pp;
+    mcl_status st = check_params(c, prm, &pp, true);
+    if (st) return st;
+    if ((st = check_csc(c, A, "A"))) return st;
+    if (!out) return fail(c, MCL_ERR_INVALID, "out is NULL");
+    if (nstages < 1 || nstages > MCL_SPLIT_MAX_STAGES)
+        return fail(c, MCL_ERR_INVALID, "nstages must be in [1, %d]", MCL_SPLIT_MAX_STAGES);
+    cudaStream_t s = (cudaStream_t)stream;
+    CUDA_TRY(c, cudaSetDevice(c->device));
+    const int64_t n = A->n;
+    if ((st = ensure_columns(c, n, s))) return st;
+    ExpandBuffers b = buffers(c);
+    const CscView Av = view(A);
+    CUDA_TRY(c, cudaMemsetAsync(c->ctr.p, 0, sizeof(DevCounters), s));
+    launch_colstats(Av, pp, b, c->num_sms, s);  // validation, column sums of A
+    if ((st = read_counters(c, s))) return st;
+    if ((st = err_flags(c, c->hctr->err))) return st;
+    int64_t stride = (int64_t)c->hctr->max_deg;
+    if (stride < MCL_SPLIT_MAX_PARTS) stride = MCL_SPLIT_MAX_PARTS;
+    stride = (stride + 31) & ~31ll;
+    const int grid_cap = 4 * c->num_sms;
+    const size_t n1 = (size_t)n + 1;
+    if (!ensure(c, c->split_bsum, n1 * 8, s) || !ensure(c, c->split_cnt, n1 * 8, s) ||
+        !ensure(c, c->split_scratch, (size_t)grid_cap * 6 * stride * 8, s))
+        return fail(c, MCL_ERR_OOM, "split scratch allocation failed");
+    double* bsum = (double*)c->split_bsum.p;
+    int64_t* cnt = (int64_t*)c->split_cnt.p;
+    launch_bsum(Av, b.colsum, bsum, s);
+    mcl_merge_stats ms{};
+    ms.stages = nstages;
+    std::vector<Part> stack;
+    int64_t live = 0;
+    auto fail_all = [&](mcl_status code, const char* what) {
+        for (auto& p : stack) free_part(c, p, s);
+        stack.clear();
+        return code == MCL_ERR_OOM ? fail(c, code, "%s: out of device memory", what) : code;
+    };
+    // count, scan, allocate and fill one product (a stage or a merge)
+    auto build = [&](RankArgs ra, bool stage, Part& P) -> mcl_status {
+        ra.n = (int32_t)n;
+        ra.scratch = c->split_scratch.p;
+        ra.stride = stride;
+        ra.grid_cap = grid_cap;
+        ra.ctr = (DevCounters*)c->ctr.p;
+        ra.nnz_out = cnt;
+        launch_split_count(ra, stage, c->num_sms, s);
+        P.colptr = (int64_t*)dev_alloc(c, n1 * 8, s);
+        if (!P.colptr) return MCL_ERR_OOM;
+        launch_exclusive_scan<int64_t>(cnt, n, P.colptr, b.scan_tmp, &b.ctr->cap_total, s);
+        if (n == 0) cudaMemsetAsync(P.colptr, 0, 8, s);
+        mcl_status e = read_counters(c, s);
+        if (e) return e;
+        if (c->hctr->err) return fail(c, MCL_ERR_INTERNAL, "split product raised flags");
+        P.nnz = n > 0 ? (int64_t)c->hctr->cap_total : 0;
+        P.rowidx = (int32_t*)dev_alloc(c, (size_t)P.nnz * 4 + 4, s);
+        P.val = (unsigned long long*)dev_alloc(c, (size_t)P.nnz * 8 + 8, s);
+        if (!P.rowidx || !P.val) return MCL_ERR_OOM;
+        if (P.nnz > 0) {
+            CUDA_TRY(c, cudaMemsetAsync(P.val, 0, (size_t)P.nnz * 8, s));
+            ra.colptr_out = P.colptr;
+            ra.row_out = P.rowidx;
+            ra.val_out = P.val;
+            launch_split_fill(ra, stage, c->num_sms, s);
+        }
+        return check_launch(c, "split product");
+    };
+    auto merge_top = [&](int count) -> mcl_status {
+        RankArgs ra{};
+        ra.nparts = count;
+        int64_t in = 0;
+        for (int q = 0; q < count; ++q) {
+            const Part& p = stack[stack.size() - 1 - q];
+            ra.pcol[q] = p.colptr;
+            ra.prow[q] = p.rowidx;
+            ra.pval[q] = p.val;
+            in += p.nnz;
+        }
+        Part M;
+        mcl_status e = build(ra, false, M);
+        if (e) {
+            free_part(c, M, s);
+            return e;
+        }
+        ms.binary_peak_entries = in > ms.binary_peak_entries ? in : ms.binary_peak_entries;
+        live += M.nnz;
+        ms.live_peak_entries = live > ms.live_peak_entries ? live : ms.live_peak_entries;
+        for (int q = 0; q < count; ++q) {
+            free_part(c, stack.back(), s);
+            stack.pop_back();
+        }
+        live -= in;
+        stack.push_back(M);
+        ++ms.merges;
+        return MCL_OK;
+    };
+    for (int t = 1; t <= nstages; ++t) {
+        RankArgs ra{};
+        ra.A = Av;
+        ra.k0 = (int32_t)((int64_t)(t - 1) * n / nstages);
+        ra.k1 = (int32_t)((int64_t)t * n / nstages);
+        ra.bsum = bsum;
+        Part P;
+        st = build(ra, true, P);
+        if (st) {
+            free_part(c, P, s);
+            return fail_all(st, "split stage failed");
+        }
+        ms.partial_entries += P.nnz;
+        stack.push_back(P);
+        live += P.nnz;
+        ms.live_peak_entries = live > ms.live_peak_entries ? live : ms.live_peak_entries;
+        // Algorithm 2: merge the top nmerges + 1 lists, nmerges = times t halves evenly
+        int nm = 0;
+        for (int jj = t; jj != 0 && (jj % 2) == 0; jj /= 2) ++nm;
+        if (nm > 0) {
+            int count = nm + 1 > (int)stack.size() ? (int)stack.size() : nm + 1;
+            while (count > 1) {  // more lists than one merge takes: merge in runs
+                const int take = count < MCL_SPLIT_MAX_PARTS ? count : MCL_SPLIT_MAX_PARTS;
+                if ((st = merge_top(take))) return fail_all(st, "merge failed");
+                count -= take - 1;
+            }
+        }
+    }
+    while (stack.size() > 1) {  // lists left when nstages is not a power of two
+        const int take = (int)stack.size() < MCL_SPLIT_MAX_PARTS ? (int)stack.size() : MCL_SPLIT_MAX_PARTS;
+        if ((st = merge_top(take))) return fail_all(st, "merge failed");
+    }
+    Part B = stack.back();
+    stack.clear();
+    ms.merged_entries = B.nnz;
+    // ---- the prune rule, inflation and renormalisation of the merged product ----
+    const CscView Bv{A->n, B.nnz, B.colptr, B.rowidx, nullptr};
+    CUDA_TRY(c, cudaMemsetAsync(c->ctr.p, 0, sizeof(DevCounters), s));
+    launch_prune_cap(Bv, pp.Krec, b, s);
+    launch_exclusive_scan<int64_t>(b.cap, n, b.off, b.scan_tmp, &b.ctr->cap_total, s);
+    if ((st = read_counters(c, s))) {
+        free_part(c, B, s);
+        return st;
+    }
+    const int64_t cap_total = (int64_t)c->hctr->cap_total;
+    if (!ensure(c, c->tmp_row, (size_t)cap_total * 4 + 4, s) ||
+        !ensure(c, c->tmp_val, (size_t)cap_total * 4 + 4, s)) {
+        free_part(c, B, s);
+        return fail(c, MCL_ERR_OOM, "scratch allocation failed");
+    }
+    b.tmp_row = (int32_t*)c->tmp_row.p;
+    b.tmp_val = (float*)c->tmp_val.p;
+    b.tmp_off0 = 0;
+    launch_prune_fixed((int32_t)n, B.colptr, B.rowidx, B.val, bsum, pp, b, c->num_sms, s);
+    launch_finalize_stats((int32_t)n, b, s);
+    int64_t* colptr_out = (int64_t*)dev_alloc(c, n1 * 8, s);
+    if (!colptr_out) {
+        free_part(c, B, s);
+        return fail(c, MCL_ERR_OOM, "output colptr allocation failed");
+    }
+    launch_exclusive_scan<int32_t>(b.kept, n, colptr_out, b.scan_tmp, &b.ctr->nnz_out, s);
+    if (n == 0) cudaMemsetAsync(colptr_out, 0, 8, s);
+    if ((st = read_counters(c, s)) || (st = err_flags(c, c->hctr->err))) {
+        free_part(c, B, s);
+        dev_free(c, colptr_out, s);
+        return st;
+    }
+    const int64_t nnz_out = n > 0 ? (int64_t)c->hctr->nnz_out : 0;
+    int32_t* row_out = (int32_t*)dev_alloc(c, (size_t)nnz_out * 4 + 4, s);
+    float* val_out = (float*)dev_alloc(c, (size_t)nnz_out * 4 + 4, s);
+    if (!row_out || !val_out) {
+        free_part(c, B, s);
+        dev_free(c, colptr_out, s);
+        dev_free(c, row_out, s);
+        dev_free(c, val_out, s);
+        return fail(c, MCL_ERR_OOM, "output allocation failed");
+    }
+    launch_compact(CscView{A->n, nnz_out, colptr_out, nullptr, nullptr}, b, colptr_out, row_out,
+                   val_out, s);
+    if ((st = check_launch(c, "split output"))) {
+        free_part(c, B, s);
+        return st;
+    }
+    CUDA_TRY(c, cudaStreamSynchronize(s));
+    free_part(c, B, s);
+    out->n = A->n;
+    out->nnz = nnz_out;
+    out->colptr = colptr_out;
+    out->rowidx = row_out;
+    out->val = val_out;
+    if (chaos) *chaos = chaos_from_bits(c->hctr->chaos_bits);
+    if (stats) *stats = ms;
+    return MCL_OK;
 }
 
 mcl_status mcl_symbolic(mcl_ctx* c, const mcl_csc* A, int64_t* flops, int64_t* nnz_out,

@@ -367,6 +367,34 @@ __device__ void block_sort_asc(uint64_t* s, int n) {
     }
 }
 
+// Fixed-point scale of a column: q = trunc(v * 2^f) with 2^f = sc1 * sc2
+// (two exact power-of-two factors, each representable in FP32).
+struct FixScale {
+    float sc1, sc2, is1, is2;
+    int f;
+    __device__ static float pow2(int e) { return __int_as_float((e + 127) << 23); }
+    __device__ void init(double s) {
+        int e = 0;
+        frexp(s > 0.0 ? s * (1.0 + 1.0 / 1048576.0) : 1.0, &e);  // s (with margin) < 2^e
+        f = 62 - e;
+        const int f1 = max(-126, min(127, f)), f2 = max(-126, min(127, f - f1));
+        sc1 = pow2(f1);
+        sc2 = pow2(f2);
+        is1 = pow2(-f1);
+        is2 = pow2(-f2);
+    }
+    __device__ __forceinline__ unsigned long long q(float aik, float akj) const {
+        const float v = __fmul_rn(aik, akj);  // the FP32 product
+        return __float2ull_rz(__fmul_rn(__fmul_rn(v, sc1), sc2));
+    }
+    __device__ __forceinline__ unsigned long long qv(float v) const {  // v: an FP32 product
+        return __float2ull_rz(__fmul_rn(__fmul_rn(v, sc1), sc2));
+    }
+    __device__ __forceinline__ float value(unsigned long long x) const {
+        return __fmul_rn(__fmul_rn(__ull2float_rn(x), is1), is2);
+    }
+};
+
 // Inflation (Alg. 1, Hadamard power r) of one FP32 value.
 __device__ __forceinline__ float inflate_value(float v, float r) {
     if (r == 2.0f) return v * v;

@@ -155,6 +155,33 @@ void launch_add_i32(const int32_t* src, int64_t m, int32_t delta, int32_t* dst, 
 void launch_place_colptr(const int64_t* colptr_g, int32_t lo, int32_t ng, int64_t base, int last,
                          int64_t* colptr, cudaStream_t s);
 
+// --- inner-dimension split and binary merge (mcl_split.cu) ---
+constexpr int MCL_SPLIT_MAX_PARTS = 32;  // partial products merged at once
+struct RankArgs {
+    CscView A;              // stage mode: the matrix
+    int32_t k0, k1;         // stage mode: the block [k0, k1) of the inner index
+    int nparts;             // merge mode: the partial products
+    const int64_t* pcol[MCL_SPLIT_MAX_PARTS];
+    const int32_t* prow[MCL_SPLIT_MAX_PARTS];
+    const unsigned long long* pval[MCL_SPLIT_MAX_PARTS];
+    int32_t n;
+    const double* bsum;     // stage mode: column sums of B (fixed-point scales)
+    void* scratch;          // per CTA: 6 * stride 8-byte slots
+    int64_t stride;         // >= the longest column of A and >= nparts
+    int grid_cap;           // CTAs the scratch holds
+    int64_t* nnz_out;       // count mode: entries per output column
+    const int64_t* colptr_out;  // fill mode
+    int32_t* row_out;
+    unsigned long long* val_out;  // fill mode: zeroed before the launch
+    DevCounters* ctr;
+};
+void launch_bsum(const CscView& A, const double* colsum, double* bsum, cudaStream_t s);
+void launch_split_count(const RankArgs& a, bool stage, int num_sms, cudaStream_t s);
+void launch_split_fill(const RankArgs& a, bool stage, int num_sms, cudaStream_t s);
+void launch_prune_fixed(int32_t n, const int64_t* colptr, const int32_t* rowidx,
+                        const unsigned long long* q, const double* bsum, const PruneParams& pp,
+                        const ExpandBuffers& b, int num_sms, cudaStream_t s);
+
 // --- estimator (mcl_estimator.cu) ---
 void launch_colmax_features(const CscView& A, int32_t iteration, const float* prev_logcf,
                             float* colmax, float* feats, cudaStream_t s,

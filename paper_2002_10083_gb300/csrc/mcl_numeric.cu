@@ -445,34 +445,6 @@ __device__ __forceinline__ int cas_shared(int* p, int cmp, int val) {
     return old;
 }
 
-// Fixed-point scale of a column: q = trunc(v * 2^f) with 2^f = sc1 * sc2
-// (two exact power-of-two factors, each representable in FP32).
-struct FixScale {
-    float sc1, sc2, is1, is2;
-    int f;
-    __device__ static float pow2(int e) { return __int_as_float((e + 127) << 23); }
-    __device__ void init(double s) {
-        int e = 0;
-        frexp(s > 0.0 ? s * (1.0 + 1.0 / 1048576.0) : 1.0, &e);  // s (with margin) < 2^e
-        f = 62 - e;
-        const int f1 = max(-126, min(127, f)), f2 = max(-126, min(127, f - f1));
-        sc1 = pow2(f1);
-        sc2 = pow2(f2);
-        is1 = pow2(-f1);
-        is2 = pow2(-f2);
-    }
-    __device__ __forceinline__ unsigned long long q(float aik, float akj) const {
-        const float v = __fmul_rn(aik, akj);  // the FP32 product
-        return __float2ull_rz(__fmul_rn(__fmul_rn(v, sc1), sc2));
-    }
-    __device__ __forceinline__ unsigned long long qv(float v) const {  // v: an FP32 product
-        return __float2ull_rz(__fmul_rn(__fmul_rn(v, sc1), sc2));
-    }
-    __device__ __forceinline__ float value(unsigned long long x) const {
-        return __fmul_rn(__fmul_rn(__ull2float_rn(x), is1), is2);
-    }
-};
-
 // Exact unsigned 32-bit division by a run-time constant d >= 1 with one
 // multiply-high (the round-up method of Granlund and Montgomery, 1994):
 // l = ceil(log2 d), m = floor(2^32 (2^l - d) / d) + 1,
@@ -1215,6 +1187,115 @@ __global__ void __launch_bounds__(PR_T) k_prune(PruneArgs2 a) {
             b.bnnz[j] = ce - cb;
         }
     }
+}
+
+// The prune rule, inflation and renormalisation of a merged product whose
+// entries are the exact 64-bit fixed-point sums of the numeric pass
+// (rows sorted per column; column j's scale from the column sum bsum[j]):
+// the statistics and keys of the numeric pass, so the same iteration.
+struct FixedChunkEnum {
+    const int32_t* rows;
+    const unsigned long long* q;
+    FixScale fx;
+    int i0, i1;
+    __device__ int count(uint64_t tau) const {
+        int c = 0;
+        for (int i = i0; i < i1; ++i) c += make_key(fx.value(q[i]), rows[i]) > tau;
+        return c;
+    }
+    __device__ void emit(uint64_t tau, uint64_t* dst, int base) const {
+        dst += base;
+        for (int i = i0; i < i1; ++i) {
+            const uint64_t k = make_key(fx.value(q[i]), rows[i]);
+            if (k > tau) *dst++ = k;
+        }
+    }
+};
+
+struct PruneFixedArgs {
+    int32_t n;
+    const int64_t* colptr;
+    const int32_t* rowidx;
+    const unsigned long long* q;
+    const double* bsum;
+    PruneParams pp;
+    ExpandBuffers b;
+};
+
+__global__ void __launch_bounds__(PR_T) k_prune_fixed(PruneFixedArgs a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int ksel = a.pp.ksel;
+    const int topcap = ksel + PR_VC;
+    uint64_t* top = reinterpret_cast<uint64_t*>(smem);
+    unsigned* hist = reinterpret_cast<unsigned*>(top + topcap);
+    unsigned long long* mhist = reinterpret_cast<unsigned long long*>(hist + 256);
+    WinShared* sh = reinterpret_cast<WinShared*>(mhist + 256);
+    const int tid = threadIdx.x;
+    const ExpandBuffers& b = a.b;
+    for (;;) {
+        if (tid == 0) sh->item = atomicAdd(&b.ctr->work_ctr, 1);
+        __syncthreads();
+        const int64_t j = sh->item;
+        __syncthreads();
+        if (j >= a.n) break;
+        const int64_t cb = a.colptr[j], ce = a.colptr[j + 1];
+        const double S = a.bsum[j];
+        FixScale fx;
+        fx.init(S);
+        int ntop = 0;
+        uint64_t tau = 0;
+        unsigned long long s_mt = 0;
+        long long s_t = 0;
+        for (int64_t base = cb; base < ce; base += PR_VC) {
+            const int cnt = (int)min((int64_t)PR_VC, ce - base);
+            const int per = (cnt + PR_T - 1) / PR_T;
+            FixedChunkEnum en{a.rowidx + base, a.q + base, fx, min(cnt, tid * per),
+                              min(cnt, tid * per + per)};
+            int c = 0;
+            for (int i = en.i0; i < en.i1; ++i) {
+                const unsigned long long qi = en.q[i];
+                const float v = fx.value(qi);
+                if (v >= a.pp.theta) {
+                    ++s_t;
+                    s_mt += qi;
+                }
+                c += make_key(v, en.rows[i]) > tau;
+            }
+            append_candidates<PR_T, 8>(en, top, topcap, ksel, ntop, tau, c, hist, sh);
+        }
+        double dv[1] = {0.0};
+        long long qv[2] = {s_t, (long long)s_mt};
+        block_sum<PR_T>(dv, 0, qv, 2, &sh->bs);
+        const double MT = ldexp((double)(unsigned long long)qv[1], -fx.f);
+        int mstar = 0;
+        double ch = 0.0;
+        const int64_t obase = b.off[j];
+        finish_column<PR_T, 8, true>(top, ntop, topcap, a.pp, S, MT, qv[0], b.cap[j],
+                                     b.tmp_row + (obase - b.tmp_off0),
+                                     b.tmp_val + (obase - b.tmp_off0), hist, mhist, sh, b.ctr, 0,
+                                     0, nullptr, &mstar, &ch);
+        if (tid == 0) {
+            b.kept[j] = mstar;
+            b.chaos[j] = ch;
+            b.bnnz[j] = ce - cb;
+        }
+    }
+}
+
+void launch_prune_fixed(int32_t n, const int64_t* colptr, const int32_t* rowidx,
+                        const unsigned long long* q, const double* bsum, const PruneParams& pp,
+                        const ExpandBuffers& b, int num_sms, cudaStream_t s) {
+    if (n == 0) return;
+    const size_t smem = (size_t)(pp.ksel + PR_VC) * 8 + 256 * 4 + 256 * 8 + sizeof(WinShared);
+    cudaFuncSetAttribute(k_prune_fixed, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int occ = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_prune_fixed, PR_T, smem);
+    if (occ < 1) occ = 1;
+    int grid = occ * num_sms;
+    if ((int64_t)grid > n) grid = (int)n;
+    cudaMemsetAsync(&b.ctr->work_ctr, 0, sizeof(int), s);
+    k_prune_fixed<<<grid, PR_T, smem, s>>>(PruneFixedArgs{n, colptr, rowidx, q, bsum, pp, b});
+    count_launches(1);
 }
 
 void launch_prune(const CscView& B, const PruneParams& pp, const ExpandBuffers& b, int num_sms,

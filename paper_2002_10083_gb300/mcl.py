@@ -63,6 +63,12 @@ class _Stats(ctypes.Structure):
                 ("alg_bytes_run", ctypes.c_int64)]
 
 
+class _MergeStats(ctypes.Structure):
+    _fields_ = [("stages", ctypes.c_int32), ("merges", ctypes.c_int32),
+                ("partial_entries", ctypes.c_int64), ("binary_peak_entries", ctypes.c_int64),
+                ("live_peak_entries", ctypes.c_int64), ("merged_entries", ctypes.c_int64)]
+
+
 _ALLOC = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
 _FREE = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)
 
@@ -76,6 +82,10 @@ SIGNATURES = {
     "mcl_last_error": (ctypes.c_char_p, [P]),
     "mcl_expand": (ctypes.c_int, [P, ctypes.POINTER(_Csc), ctypes.POINTER(_Params),
                                   ctypes.POINTER(_Csc), ctypes.POINTER(ctypes.c_double), P]),
+    "mcl_expand_split": (ctypes.c_int, [P, ctypes.POINTER(_Csc), ctypes.POINTER(_Params),
+                                        ctypes.c_int32, ctypes.POINTER(_Csc),
+                                        ctypes.POINTER(ctypes.c_double),
+                                        ctypes.POINTER(_MergeStats), P]),
     "mcl_prune_select_recover": (ctypes.c_int, [P, ctypes.POINTER(_Csc), ctypes.POINTER(_Params),
                                                 ctypes.POINTER(_Csc), P]),
     "mcl_inflate_normalize": (ctypes.c_int, [P, ctypes.POINTER(_Csc), ctypes.c_float, P]),
@@ -271,6 +281,20 @@ class Context:
         self._check(self.lib.mcl_expand(self.h, ctypes.byref(a), ctypes.byref(p),
                                         ctypes.byref(out), ctypes.byref(ch), _stream_ptr(stream)))
         return self._adopt_csc(out), ch.value
+
+    def expand_split(self, A: DeviceCSC, prm: Params, nstages: int, stream=None):
+        """One MCL iteration with the inner dimension split into `nstages`
+        blocks and the partial products binary-merged -> (A_next, chaos, stats)."""
+        a = A.c()
+        p = prm.c()
+        out = _Csc()
+        ch = ctypes.c_double(0.0)
+        ms = _MergeStats()
+        self._check(self.lib.mcl_expand_split(self.h, ctypes.byref(a), ctypes.byref(p),
+                                              int(nstages), ctypes.byref(out), ctypes.byref(ch),
+                                              ctypes.byref(ms), _stream_ptr(stream)))
+        stats = {name: getattr(ms, name) for name, _ in _MergeStats._fields_}
+        return self._adopt_csc(out), ch.value, stats
 
     def prune_select_recover(self, B: DeviceCSC, prm: Params, stream=None) -> DeviceCSC:
         b = B.c()
