@@ -30,8 +30,10 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 DEFAULT_WEIGHTS = os.path.join(HERE, "estimator_mix.npz")
 # the default mixed training and held-out sets: workload, keyword arguments, seeds
 TRAIN_MIX = "zipf1m:n=100000:1-3,zipf1m:n=200000:1-3,zipf1m:n=400000:1-3,zipf1m:1-6," \
-            "zipf4m:n=1000000:1-2,batch4096:ncomp=256:1-6"
-EVAL_MIX = "zipf1m:n=400000:100-101,zipf1m:100-101,batch4096:ncomp=256:100-101"
+            "zipf4m:n=1000000:1-2,batch4096:ncomp=64:1-3,batch4096:ncomp=256:1-4," \
+            "batch4096:ncomp=1024:1-2"
+EVAL_MIX = "zipf1m:n=400000:100-101,zipf1m:100-101,batch4096:ncomp=128:100-101," \
+           "batch4096:ncomp=256:100-101"
 NH = 64
 SHAPES = [("W1", (NH, mcl.NFEATURES)), ("b1", (NH,)), ("W2", (NH, NH)), ("b2", (NH,)),
           ("W3", (2, NH)), ("b3", (2,))]
