@@ -680,14 +680,23 @@ __global__ void __launch_bounds__(T, MINB) k_expand(ExpandArgs a) {
                     const int32_t* rows = A.rowidx + ks;
                     const float* vv = A.val + ks;
                     const float akj = meta.akj[kidx];
+                    // the next 128 products are loaded while this chunk is routed
+                    int rr[4];
+                    float pv[4];
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        const int p = 32 * c + lane;
+                        rr[c] = p < len ? __ldg(rows + p) : 0;
+                        pv[c] = p < len ? __ldg(vv + p) : 0.0f;
+                    }
                     for (int pb = 0; pb < len; pb += 128) {
-                        int rr[4];
-                        float pv[4];
+                        int nr[4];
+                        float nv[4];
 #pragma unroll
                         for (int c = 0; c < 4; ++c) {
-                            const int p = pb + 32 * c + lane;
-                            rr[c] = p < len ? __ldg(rows + p) : 0;
-                            pv[c] = p < len ? __ldg(vv + p) : 0.0f;
+                            const int p = pb + 128 + 32 * c + lane;
+                            nr[c] = p < len ? __ldg(rows + p) : 0;
+                            nv[c] = p < len ? __ldg(vv + p) : 0.0f;
                         }
 #pragma unroll
                         for (int c = 0; c < 4; ++c) {
@@ -715,6 +724,11 @@ __global__ void __launch_bounds__(T, MINB) k_expand(ExpandArgs a) {
                                 if (capw == 0 || pos < ((int)w + 1) * capw)
                                     bkt[pos] = make_int2(row, __float_as_int(pv[c] * akj));
                             }
+                        }
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) {
+                            rr[c] = nr[c];
+                            pv[c] = nv[c];
                         }
                     }
                 }
@@ -872,23 +886,31 @@ __global__ void __launch_bounds__(T, MINB) k_expand(ExpandArgs a) {
             // ---- 1. insert the products of the window ----
             if (bucket) {
                 const int bs = woff[F0], be = wlim[F0];
-                // four products per lane in flight before the table updates
-                for (int pb = bs + warp * 128; pb < be; pb += T * 4) {
-                    int rr[4];
-                    float pv[4];
+                // four products per lane in flight while the previous four update
+                // the table (the loads are issued before the shared atomics)
+                int2 cx[4];
+                int pb = bs + warp * 128;
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int p = pb + 32 * u + lane;
+                    cx[u] = p < be ? bkt[p] : make_int2(-1, 0);
+                }
+                for (; pb < be; pb += T * 4) {
+                    int2 nx[4];
 #pragma unroll
                     for (int u = 0; u < 4; ++u) {
-                        const int p = pb + 32 * u + lane;
-                        const int2 x = p < be ? bkt[p] : make_int2(-1, 0);
-                        rr[u] = x.x;
-                        pv[u] = __int_as_float(x.y);
+                        const int p = pb + T * 4 + 32 * u + lane;
+                        nx[u] = p < be ? bkt[p] : make_int2(-1, 0);
                     }
 #pragma unroll
                     for (int u = 0; u < 4; ++u) {
-                        bool valid = rr[u] >= 0;
-                        if (RS) valid = valid && rr[u] >= R0 && rr[u] < R1;
-                        if (valid) add(rr[u], fx.qv(pv[u]));
+                        const int row = cx[u].x;
+                        bool valid = row >= 0;
+                        if (RS) valid = valid && row >= R0 && row < R1;
+                        if (valid) add(row, fx.qv(__int_as_float(cx[u].y)));
                     }
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) cx[u] = nx[u];
                 }
             } else if (lane_mode) {
                 for (int kidx = tid; kidx < d; kidx += T) {
