@@ -468,18 +468,38 @@ def run_batched(args):
     torch.cuda.synchronize()
     peak, peak_kind = _peaks()
 
-    def timed_run(graph: int, batched: int, use_est: int):
+    # pinned host copies of A and of the labels for the end-to-end measurement
+    host = None
+    if not args.no_e2e:
+        host = (torch.from_numpy(np.ascontiguousarray(A32.colptr, np.int64)).pin_memory(),
+                torch.from_numpy(np.ascontiguousarray(A32.rowidx, np.int32)).pin_memory(),
+                torch.from_numpy(np.ascontiguousarray(A32.val, np.float32)).pin_memory(),
+                torch.empty(A.n, dtype=torch.int32).pin_memory())
+    e2e = {}
+
+    def timed_run(graph: int, batched: int, use_est: int, with_e2e: bool = False):
         ctx.set_option(mcl.OPT_GRAPH, graph)
         p = mcl.Params(threshold=1e-4, select_k=1100, recover_pct=0.9, inflation=2.0,
                        chaos_eps=1e-3, max_iters=args.max_iters, batched=batched,
                        use_estimator=use_est)
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        ev[0].record()
+        if with_e2e:  # the input from pinned host memory, inside the timed region
+            D.colptr.copy_(host[0], non_blocking=True)
+            D.rowidx.copy_(host[1], non_blocking=True)
+            D.val.copy_(host[2], non_blocking=True)
+        ev[1].record()
         out = ctx.run(D, p, comp_offsets=offs, keep_final=False)
-        e1.record()
+        ev[2].record()
+        if with_e2e:  # the labels back to the host
+            host[3].copy_(out[0], non_blocking=True)
+        ev[3].record()
         torch.cuda.synchronize()
-        return out, e0.elapsed_time(e1), ctx.stats()
+        if with_e2e:
+            e2e["ms"] = ev[0].elapsed_time(ev[3])
+            e2e["h2d_ms"] = ev[0].elapsed_time(ev[1])
+            e2e["d2h_ms"] = ev[2].elapsed_time(ev[3])
+        return out, ev[1].elapsed_time(ev[2]), ctx.stats()
 
     def summary(res, ms, st):
         lab_, iters_, hist_, _, nc_ = res
@@ -495,18 +515,22 @@ def run_batched(args):
     # CUDA graph replays), the same with exact sizing, and plain: exact sizing,
     # eager, no per-component retirement (each group of components iterates until
     # the group's chaos < eps)
-    runs = [("learned_batched", 1, 1, 1), ("batched_exact", 1, 1, 0), ("plain", 0, 0, 0)]
+    wanted = args.forms.split(",")
+    runs = [r for r in [("learned_batched", 1, 1, 1), ("batched_exact", 1, 1, 0), ("plain", 0, 0, 0)]
+            if r[0] in wanted or r[0] == "learned_batched"]
     results, forms = {}, {}
     clocks = None
     for name, graph, batched, ue in runs:
         if name == "learned_batched":
-            (res, ms, st), clocks = _clocked(lambda: timed_run(graph, batched, ue))
+            (res, ms, st), clocks = _clocked(
+                lambda: timed_run(graph, batched, ue, with_e2e=host is not None))
         else:
             res, ms, st = timed_run(graph, batched, ue)
         results[name] = res
         forms[name] = summary(res, ms, st)
     lab = results["learned_batched"][0].cpu().numpy()
-    labels_equal = bool(np.array_equal(lab, results["batched_exact"][0].cpu().numpy()))
+    labels_equal = {k: bool(np.array_equal(lab, results[k][0].cpu().numpy()))
+                    for k in results if k != "learned_batched"}
     parity = None if args.no_check else check_batch(ctx, A32, offs, lab, results, args)
     cpu = None if args.no_cpu_baseline else batch_cpu_baseline(A32, offs, args.cpu_seconds)
     main = forms["learned_batched"]
@@ -516,9 +540,18 @@ def run_batched(args):
             "n": A.n, "nnz": A.nnz, "components": len(offs) - 1,
             "value": main["iters_per_s"], "unit": "MCL iters/s", "higher_is_better": True,
             "form": "learned_batched", "forms": forms,
-            "speedup_learned_batched_vs_plain": round(forms["plain"]["seconds"] / main["seconds"], 4),
-            "speedup_learned_vs_exact_batched": round(forms["batched_exact"]["seconds"] / main["seconds"], 4),
-            "labels_learned_equal_exact": labels_equal,
+            "speedup_learned_batched_vs_plain": (round(forms["plain"]["seconds"] / main["seconds"], 4)
+                                                 if "plain" in forms else None),
+            "speedup_learned_vs_exact_batched": (round(forms["batched_exact"]["seconds"] / main["seconds"], 4)
+                                                 if "batched_exact" in forms else None),
+            "labels_learned_equal": labels_equal,
+            "e2e": None if not e2e else {
+                "value": round(main["iterations"] / (e2e["ms"] / 1000.0), 4), "unit": "MCL iters/s",
+                "h2d_bytes_per_step": int((A.n + 1) * 8 + A.nnz * 8),
+                "d2h_bytes_per_step": int(A.n * 4), "seconds": round(e2e["ms"] / 1000.0, 2),
+                "h2d_ms": round(e2e["h2d_ms"], 1), "d2h_ms": round(e2e["d2h_ms"], 1),
+                "vs_device_run": round(e2e["ms"] / 1000.0 / main["seconds"], 4),
+                "how": "pinned host buffers: H2D of A, the whole run, D2H of the labels"},
             "roofline": {"bound": "hbm", "achieved": round(main["hbm_frac_alg"] * peak, 1),
                          "peak": peak, "unit": "GB/s", "frac": main["hbm_frac_alg"],
                          "kernel": "whole run (algorithmic bytes of every iteration / run time)",
@@ -550,7 +583,9 @@ def check_batch(ctx, A, offs, lab, results, args):
     sizes = np.diff(offs)
     rng = np.random.default_rng(7)
     small = np.nonzero(sizes <= 300)[0]
-    pick = rng.choice(small, min(64, len(small)), replace=False)
+    medium = np.nonzero((sizes > 300) & (sizes <= 5000))[0]
+    pick = np.concatenate([rng.choice(small, min(64, len(small)), replace=False),
+                           rng.choice(medium, min(8, len(medium)), replace=False)]).astype(np.int64)
     big = int(np.argmax(sizes))
     mism = []
     for c in pick:
@@ -578,11 +613,19 @@ def check_batch(ctx, A, offs, lab, results, args):
     lab1, *_ = ctx.run(mcl.DeviceCSC.from_host(sub), p1, keep_final=False)
     big_same = bool(np.array_equal(lab1.cpu().numpy(), lab[lo:hi] - lo))
     torch.cuda.synchronize()
+    # the largest component's clusters from the oracle's whole loop
+    tb = time.time()
+    _, it_big, _, lab_big = oracle.run_mcl(sub, oprm)
+    big_oracle = bool(np.array_equal(lab[lo:hi] - lo, lab_big))
+    big_oracle_s = time.time() - tb
     return {"sampled_components": len(pick), "sampled_max_size": int(sizes[pick].max()),
             "clusters_equal_oracle": len(pick) - len(mism), "mismatched_components": mism,
             "largest_component": {"size": int(hi - lo), "iterations_checked": 3,
                                   "columns_checked": big_cols, "values_within_1e-5": big_ok,
-                                  "batched_labels_equal_alone": big_same},
+                                  "batched_labels_equal_alone": big_same,
+                                  "clusters_equal_oracle": big_oracle,
+                                  "oracle_iterations": int(it_big),
+                                  "oracle_seconds": round(big_oracle_s, 1)},
             "seconds": round(time.time() - t0, 1)}
 
 
@@ -723,6 +766,52 @@ def run_planted(args):
     return 0
 
 
+def run_split(args):
+    """One MCL iteration of the power-law graph through mcl_expand and through
+    the split expansion with the binary merge (Section IV, Algorithm 2): time,
+    equality, and the merge's memory against a multiway merge's."""
+    import torch
+    from paper_2002_10083_gb300 import mcl
+    n = args.n or 100_000
+    A = make_workload("zipf1m", n=n)
+    D = mcl.DeviceCSC.from_host(A)
+    ctx = mcl.Context(0)
+    prm = mcl.Params(threshold=1e-4, select_k=1100, recover_pct=0.9, inflation=2.0)
+
+    def timed(fn):
+        fn()  # warm
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        r = fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return r, e0.elapsed_time(e1)
+
+    (ref, _), ms_ref = timed(lambda: ctx.expand(D, prm))
+    flops = int(ctx.stats()["flops"])
+    rows = []
+    for ns in (4, 8, 16):
+        (out, _, st), ms = timed(lambda: ctx.expand_split(D, prm, ns))
+        same = (torch.equal(out.colptr, ref.colptr) and torch.equal(out.rowidx, ref.rowidx)
+                and torch.equal(out.val.view(torch.int32), ref.val.view(torch.int32)))
+        rows.append({"stages": ns, "ms": round(ms, 1), "equal_to_one_pass": bool(same),
+                     "merges": st["merges"], "multiway_entries": st["partial_entries"],
+                     "binary_peak_entries": st["binary_peak_entries"],
+                     "binary_saving": round(1.0 - st["binary_peak_entries"] / max(1, st["partial_entries"]), 4),
+                     "live_peak_entries": st["live_peak_entries"],
+                     "merged_entries": st["merged_entries"]})
+        del out
+    line = {"metric": "split expansion with binary merge vs one pass", "workload":
+            f"zipf1m graph family at n={n}: one MCL iteration (K 1100, theta 1e-4, p 0.9, r 2)",
+            "n": A.n, "nnz": A.nnz, "multiply_adds": flops, "one_pass_ms": round(ms_ref, 1),
+            "bytes_per_entry": 12, "stages": rows}
+    print(json.dumps(line), flush=True)
+    ctx.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -743,6 +832,8 @@ def main():
     ap.add_argument("--group-budget-gb", type=float, default=150.0,
                     help="device bytes per group of components for batch4096 (0: one group)")
     ap.add_argument("--no-check", action="store_true", help="skip the batch4096 oracle checks")
+    ap.add_argument("--forms", default="learned_batched,batched_exact,plain",
+                    help="batch4096 forms to time (learned_batched always runs)")
     ap.add_argument("--bucket-budget-gb", type=float, default=0.0,
                     help="device memory of the numeric pass's product buckets (0: library default)")
     args = ap.parse_args()
@@ -754,6 +845,8 @@ def main():
         return run_batched(args)
     if args.workload == "planted2k":
         return run_planted(args)
+    if args.workload == "zipf_split":
+        return run_split(args)
     return run_gpu(args)
 
 
