@@ -105,9 +105,10 @@ __global__ void k_colstats(CscView A, int32_t Krec, ExpandBuffers b) {
             b.rhi[j] = any ? mx : -1;
             long long cap = f < (long long)span ? f : (long long)span;
             if (cap > Krec) cap = Krec;
-            if (b.active && !b.active[j]) cap = ce - cb;  // carried column: copied as is
+            const bool carried = b.active && !b.active[j];
+            if (carried) cap = ce - cb;  // carried column: copied as is
             b.cap[j] = cap;
-            fl_acc += (unsigned long long)f;
+            if (!carried) fl_acc += (unsigned long long)f;  // multiply-adds of this iteration
             fl_max = fl_max > (unsigned long long)f ? fl_max : (unsigned long long)f;
             deg_max = max(deg_max, (int)(ce - cb));
             span_max = max(span_max, span);
@@ -845,10 +846,12 @@ void launch_staging_guard(DevCounters* ctr, int64_t capacity, cudaStream_t s) {
 // as a matrix of its own (rows re-based), and the way back
 // ---------------------------------------------------------------------------
 
-// colptr_g[i] = colptr[lo + i] - colptr[lo] for i in [0, ng]
+// colptr_g[i] = colptr[lo + i] - colptr[lo] for i in [0, ng] (grid-stride:
+// the grid is capped)
 __global__ void k_block_colptr(const int64_t* colptr, int32_t lo, int32_t ng, int64_t* colptr_g) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i <= ng) colptr_g[i] = colptr[lo + i] - colptr[lo];
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i <= ng;
+         i += (int64_t)gridDim.x * blockDim.x)
+        colptr_g[i] = colptr[lo + i] - colptr[lo];
 }
 
 // dst[p] = src[p] + delta for p in [0, m)
@@ -862,8 +865,10 @@ __global__ void k_add_i32(const int32_t* src, int64_t m, int32_t delta, int32_t*
 // when last)
 __global__ void k_place_colptr(const int64_t* colptr_g, int32_t lo, int32_t ng, int64_t base,
                                int last, int64_t* colptr) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < ng || (last && i == ng)) colptr[lo + i] = colptr_g[i] + base;
+    const int64_t end = last ? (int64_t)ng + 1 : (int64_t)ng;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < end;
+         i += (int64_t)gridDim.x * blockDim.x)
+        colptr[lo + i] = colptr_g[i] + base;
 }
 
 static unsigned grid_for(int64_t m) {

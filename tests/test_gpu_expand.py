@@ -475,6 +475,68 @@ def test_batched_groups_equal_one_run(ctx):
     assert it1 == max(o_iters) and np.array_equal(lab1.cpu().numpy(), o_lab)
 
 
+@pytest.mark.parametrize("graph", [0, 1])
+def test_batched_flops_count_only_active_components(ctx, graph):
+    """A batched run's multiply-adds are those of each component's own
+    iterations up to and including the one where it converged (retired
+    components are carried, not expanded), eager and as graph replays."""
+    from paper_2002_10083_gb300 import mcl
+    A = synth.component_batch(ncomp=8, size_lo=50, size_hi=600, p_in=0.3, p_out=0.002,
+                              seed=9).with_val32()
+    offs = A.comp_offsets
+    prm = _prm(theta=1e-4, K=200, p=0.9, iters=40)
+    prm.batched = 1
+    try:
+        ctx.set_option(mcl.OPT_GRAPH, graph)
+        _, iters, _, _, nc = ctx.run(_dev(A), prm, comp_offsets=offs, keep_final=False)
+        got = ctx.stats()["flops_run"]
+    finally:
+        ctx.set_option(mcl.OPT_GRAPH, 1)  # the library default
+    assert not nc
+    want, longest = 0, 0
+    for c in range(len(offs) - 1):
+        D = _dev(oracle.submatrix(A, int(offs[c]), int(offs[c + 1])))
+        for it in range(iters):
+            D, ch = ctx.expand(D, prm)
+            want += ctx.stats()["flops"]
+            if ch < prm.chaos_eps:
+                break
+        longest = max(longest, it + 1)
+    assert longest == iters
+    assert got == want
+
+
+def test_batched_groups_wider_than_one_launch_grid(ctx):
+    """Groups of 1.4M columns each (more than the 1,245,184 threads of a
+    capped launch grid): every group's column pointers are re-based and
+    placed back in full, and the result equals the single-group run.
+    700,000 disjoint 4-cliques with uniform weights are a fixed point of the
+    iteration, so the clusters are the cliques."""
+    from paper_2002_10083_gb300 import mcl
+    m, ncl = 4, 700_000
+    n = m * ncl
+    base = (np.arange(n, dtype=np.int64) // m) * m
+    A = synth.CSC(n=n, colptr=np.arange(n + 1, dtype=np.int64) * m,
+                  rowidx=(np.repeat(base, m) + np.tile(np.arange(m), n)).astype(np.int32),
+                  val=np.full(n * m, 1.0 / m)).with_val32()
+    offs = np.array([0, n // 2, n], np.int32)
+    prm = _prm(theta=1e-4, K=100, p=0.9, iters=5)
+    prm.batched = 1
+    lab0, it0, _, F0, nc0 = ctx.run(_dev(A), prm, comp_offsets=offs)
+    assert ctx.stats()["groups"] == 1
+    try:
+        ctx.set_option(mcl.OPT_GROUP_BUDGET, 6 << 30)
+        lab1, it1, _, F1, nc1 = ctx.run(_dev(A), prm, comp_offsets=offs)
+        groups = ctx.stats()["groups"]
+    finally:
+        ctx.set_option(mcl.OPT_GROUP_BUDGET, 0)
+    assert groups == 2
+    assert not nc0 and not nc1 and it0 == it1 == 1
+    assert np.array_equal(lab1.cpu().numpy(), base.astype(np.int32))
+    assert np.array_equal(lab0.cpu().numpy(), lab1.cpu().numpy())
+    _assert_same(F1, F0)
+
+
 @pytest.mark.parametrize("learned", [False, True])
 def test_batched_graph_replay_every_iteration_matches_oracle(ctx, learned):
     """Every replayed iteration of a batched run against the oracle fed the
