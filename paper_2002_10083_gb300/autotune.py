@@ -164,6 +164,11 @@ def main(argv=None) -> int:
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--select-k", type=int, default=1100)
     ap.add_argument("--out", default=TABLE_PATH)
+    ap.add_argument("--record-class", default=None,
+                    help="record the winner under this workload class instead of the input's "
+                         "(a larger member of the same graph family)")
+    ap.add_argument("--from-iteration", type=int, default=1,
+                    help="time the expansion of A_{k-1} (k > 1: after k - 1 default iterations)")
     args = ap.parse_args(argv)
     kw = {}
     if args.n:
@@ -174,9 +179,12 @@ def main(argv=None) -> int:
     D = mcl.DeviceCSC.from_host(A)
     ctx = mcl.Context(0)
     prm = mcl.Params(threshold=1e-4, select_k=args.select_k, recover_pct=0.9, inflation=2.0)
+    wc = args.record_class or class_of_host(A)  # the class of the input the run starts from
+    for _ in range(args.from_iteration - 1):
+        D, _ = ctx.expand(D, prm)
     res = tune(ctx, D, prm, reps=args.reps)
+    res["from_iteration"] = args.from_iteration
     dev = torch.cuda.get_device_name(0)
-    wc = class_of_host(A)
     table = record(load(args.out), dev, wc, res)
     save(table, args.out)
     print(json.dumps({"device": dev, "class": wc, "workload": args.workload, **res}))
