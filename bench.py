@@ -462,7 +462,7 @@ def run_batched(args):
     est_path = args.estimator or estimator.DEFAULT_WEIGHTS
     est_meta = estimator.install(ctx, est_path)
     tuned = autotune.apply(ctx, autotune.load(), torch.cuda.get_device_name(0),
-                           autotune.class_of_host(A))
+                           args.tuning_class or autotune.class_of_host(A))
     if args.group_budget_gb:
         ctx.set_option(mcl.OPT_GROUP_BUDGET, int(args.group_budget_gb * (1 << 30)))
     torch.cuda.synchronize()
@@ -559,6 +559,7 @@ def run_batched(args):
             "parity": parity, "cpu_baseline": cpu, "clocks": clocks,
             "generation_s": round(gen_s, 1), "group_budget_gb": args.group_budget_gb,
             "tuning": tuned if tuned is not None else "library defaults",
+            "tuning_class": args.tuning_class or autotune.class_of_host(A),
             "estimator": {"weights": os.path.basename(est_path),
                           "trained_on": est_meta.get("workload"),
                           "train_seeds": est_meta.get("train_seeds")}}
@@ -832,6 +833,9 @@ def main():
     ap.add_argument("--group-budget-gb", type=float, default=150.0,
                     help="device bytes per group of components for batch4096 (0: one group)")
     ap.add_argument("--no-check", action="store_true", help="skip the batch4096 oracle checks")
+    ap.add_argument("--tuning-class", default=None,
+                    help="batch4096: apply the autotuner's setting stored for this workload class "
+                         "(e.g. one tuned on a smaller batch of the same family)")
     ap.add_argument("--forms", default="learned_batched,batched_exact,plain",
                     help="batch4096 forms to time (learned_batched always runs)")
     ap.add_argument("--bucket-budget-gb", type=float, default=0.0,
