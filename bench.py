@@ -560,6 +560,7 @@ def run_batched(args):
             "generation_s": round(gen_s, 1), "group_budget_gb": args.group_budget_gb,
             "tuning": tuned if tuned is not None else "library defaults",
             "tuning_class": args.tuning_class or autotune.class_of_host(A),
+            "workload_class": autotune.class_of_host(A),
             "estimator": {"weights": os.path.basename(est_path),
                           "trained_on": est_meta.get("workload"),
                           "train_seeds": est_meta.get("train_seeds")}}
