@@ -673,7 +673,7 @@ def run_zipf4m(args):
     ctx = mcl.Context(0)
     est_meta = estimator.install(ctx, args.estimator or estimator.DEFAULT_WEIGHTS)
     tuned = autotune.apply(ctx, autotune.load(), torch.cuda.get_device_name(0),
-                           autotune.class_of_host(A))
+                           args.tuning_class or autotune.class_of_host(A))
     budget = args.phase_budget_gb or 180.0
     ctx.set_option(mcl.OPT_PHASE_BUDGET, int(budget * (1 << 30)))
     peak, peak_kind = _peaks()
@@ -717,6 +717,7 @@ def run_zipf4m(args):
             "seconds": round(tot_ms / 1000.0, 2), "per_iteration": iters, "clocks": clocks,
             "generation_s": round(gen_s, 1), "phase_budget_gb": budget,
             "tuning": tuned if tuned is not None else "library defaults",
+            "tuning_class": args.tuning_class or autotune.class_of_host(A),
             "estimator": {"trained_on": est_meta.get("workload"), "train_seeds": est_meta.get("train_seeds")}}
     print(json.dumps(line), flush=True)
     ctx.close()
