@@ -303,7 +303,12 @@ mcl_status mcl_set_option(mcl_ctx* ctx, int option, int64_t value);
 #define MCL_NFEATURES 16
 
 /* Install estimator weights (host arrays; copied) and the safety factor s
- * (estimate = ceil(expm1(y0) * s), clamped to [1, min(flops_j, span_j)]). */
+ * (estimate = ceil(expm1(y0) * s), clamped to [1, min(flops_j, span_j)]).
+ * The weights come as arrays, not as a file path, so that the library does
+ * no file I/O and needs no archive format: a caller reads its weight file
+ * (the Python binding reads a .npz) and passes the BF16 bit patterns
+ * (5378 values, layout as in the training kernels) and the standardisation
+ * (16 means, then 16 standard deviations). */
 mcl_status mcl_estimator_load(mcl_ctx* ctx, const uint16_t* w_bf16_host, const float* norm_host,
                               float safety);
 
