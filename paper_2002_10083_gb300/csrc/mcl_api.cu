@@ -464,6 +464,7 @@ static mcl_status expand_impl(mcl_ctx* c, const mcl_csc* A, const mcl_params* pr
                 const int64_t maxf = (int64_t)c->hctr->max_flops;
                 int64_t capb = (int64_t)(c->bucket_budget / ((size_t)g * 8));
                 if (capb > maxf) capb = maxf;
+                if (capb > (int64_t)1 << 30) capb = (int64_t)1 << 30;  // int32 bucket positions
                 if (capb >= 1024 && ensure(c, c->bucket_row, (size_t)g * capb * 8, s) &&
                     ensure(c, c->woff, (size_t)g * 2 * (WINDOW_MAX + 1) * 4, s)) {
                     bq.bucket_row = (int32_t*)c->bucket_row.p;
@@ -1180,6 +1181,7 @@ static void static_iteration(mcl_ctx* c, const mcl_params* prm, const PruneParam
             bq.bucket_row = (int32_t*)c->bucket_row.p;
             bq.woff = (int32_t*)c->woff.p;
             bq.bucket_cap = (int64_t)(c->bucket_row.bytes / ((size_t)g * 8));
+            if (bq.bucket_cap > (int64_t)1 << 30) bq.bucket_cap = (int64_t)1 << 30;
         }
         launch_numeric(q, Av, pp, bq, g, s);
     }
